@@ -1,0 +1,335 @@
+"""Physics pins of the oracle: samplers against analytic distributions, transport against
+closed forms, single interactions against kinematic identities, runs against invariants."""
+import numpy as np
+import pytest
+from scipy import integrate, stats
+
+import oracle
+from paper_2302_08252_gb300 import workloads as W
+
+MC2 = 0.51099895
+KC = 0.01
+
+
+def kn_dsig_deps(eps, k):
+    """Textbook Klein-Nishina dsigma/deps (up to the constant pi r_e^2 / k)."""
+    cost = 1.0 - (1.0 - eps) / (k * eps)
+    return eps + 1.0 / eps - (1.0 - cost * cost)
+
+
+@pytest.mark.parametrize("k", [0.02, 0.2, 2.0, 20.0, 2000.0])
+def test_klein_nishina_sampler_chi2(k):
+    n = 200_000
+    ids = np.arange(n, dtype=np.uint64) + (np.uint64(9) << np.uint64(32))
+    eps, att = oracle.compton_eps(k, ids, seed=11, event=3, step=5)
+    assert att.max() < 64
+    e0 = 1.0 / (1.0 + 2.0 * k)
+    edges = np.linspace(e0, 1.0, 51)
+    obs, _ = np.histogram(eps.astype(np.float64), bins=edges)
+    w = np.array([integrate.quad(kn_dsig_deps, a, b, args=(k,), epsrel=1e-11)[0]
+                  for a, b in zip(edges[:-1], edges[1:])])
+    exp = n * w / w.sum()
+    chi2 = ((obs - exp) ** 2 / exp).sum()
+    p = stats.chi2.sf(chi2, df=49)
+    assert p > 1e-3, (chi2, p)
+
+
+def _photon(world, e, d=(0.0, 0.0, 1.0), nia=0.0, id=0, slab=0, z=None, x=0.0, y=0.0):
+    z = world_plane(world, slab) + 0.5 if z is None else z
+    return oracle.make_track(x=x, y=y, z=z, d=d, e=e, nia=nia, id=id, slab=slab)
+
+
+def world_plane(world, slab):
+    return float(np.cumsum(np.concatenate([[0.0], world._keep[0]]))[slab])
+
+
+def _unit(rng, n):
+    v = rng.normal(size=(n, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def test_brem_spectrum_ks(oworld):
+    t0 = 1000.0
+    ks = []
+    for i in range(20000):
+        r = oracle.step_one(oworld, W.E_MINUS, _photon(oworld, t0, id=i))
+        assert r["proc"] == oracle.PROC_BREM and r["lim"] == oracle.LIM_PHYS
+        assert r["sec_type"][0] == W.GAMMA
+        k = float(r["sec"][0]["e"])
+        assert KC <= k <= t0
+        assert r["track"]["e"] == np.float32(np.float32(t0) - np.float32(k))
+        ks.append(k)
+    ks = np.array(ks)
+    cdf = lambda k: np.log(k / KC) / np.log(t0 / KC)
+    assert stats.kstest(ks, cdf).pvalue > 1e-3
+
+
+def test_compton_kinematics_and_azimuth(oworld):
+    rng = np.random.default_rng(5)
+    dirs = _unit(rng, 6000)
+    phis, n_c = [], 0
+    for i, d in enumerate(dirs):
+        e = 2.0
+        r = oracle.step_one(oworld, W.GAMMA, _photon(oworld, e, d=tuple(d), id=i))
+        if r["proc"] != oracle.PROC_COMPTON:
+            continue
+        n_c += 1
+        t = r["track"]
+        e1 = float(t["e"])
+        d1 = np.array([t["dx"], t["dy"], t["dz"]], np.float64)
+        d0 = np.array(d, np.float32).astype(np.float64)
+        cos_k = 1.0 - MC2 * (1.0 / e1 - 1.0 / e)       # Compton formula
+        assert np.dot(d0, d1) == pytest.approx(cos_k, abs=2e-5)
+        assert np.linalg.norm(d1) == pytest.approx(1.0, abs=2e-6)
+        if r["nsec"]:
+            s = r["sec"][0]
+            de = np.array([s["dx"], s["dy"], s["dz"]], np.float64)
+            assert float(s["e"]) == pytest.approx(e - e1, rel=1e-6)
+            p = e * d0 - e1 * d1
+            assert np.dot(de, p / np.linalg.norm(p)) == pytest.approx(1.0, abs=1e-5)
+        # azimuth of d1 about d0 in a fixed frame
+        a = np.cross(d0, [0.0, 0.0, 1.0] if abs(d0[2]) < 0.9 else [1.0, 0.0, 0.0])
+        a /= np.linalg.norm(a)
+        b = np.cross(d0, a)
+        perp = d1 - np.dot(d1, d0) * d0
+        if np.linalg.norm(perp) > 1e-3:
+            phis.append(np.arctan2(np.dot(perp, b), np.dot(perp, a)))
+    assert n_c > 3000
+    phis = (np.array(phis) + np.pi) / (2 * np.pi)
+    assert stats.kstest(phis, "uniform").pvalue > 1e-3
+
+
+def test_photon_process_fractions(oworld):
+    # at 20 MeV in lead all three processes compete; fractions follow the cross sections
+    e, n = 20.0, 20000
+    procs = np.array([oracle.step_one(oworld, W.GAMMA, _photon(oworld, e, id=i))["proc"]
+                      for i in range(n)])
+    sc, sp, se = (oracle.sigma(k, 0, e) for k in ("compton", "pair", "phot"))
+    tot = sc + sp + se
+    for proc, s in ((oracle.PROC_COMPTON, sc), (oracle.PROC_PAIR, sp), (oracle.PROC_PHOT, se)):
+        f = np.mean(procs == proc)
+        p = s / tot
+        assert abs(f - p) < 4 * np.sqrt(p * (1 - p) / n) + 2e-3 * p, (proc, f, p)
+
+
+def test_pair_and_photoelectric_kinematics(oworld):
+    for i in range(3000):
+        e = 50.0
+        r = oracle.step_one(oworld, W.GAMMA, _photon(oworld, e, id=i))
+        if r["proc"] == oracle.PROC_PAIR:
+            assert r["alive"] == 0 and r["death"] == oracle.DEATH_ABSORB
+            es = sum(float(s["e"]) for s in r["sec"] if s["e"] != np.float32(MC2)) + r["cut"]
+            assert es == pytest.approx(e - 2 * MC2, rel=1e-6)
+            assert r["mc"] == pytest.approx(2 * MC2, rel=1e-5)
+            for s, ty in zip(r["sec"], r["sec_type"]):
+                if ty != W.GAMMA:
+                    assert (s["dx"], s["dy"], s["dz"]) == (0.0, 0.0, 1.0)
+        elif r["proc"] == oracle.PROC_PHOT:
+            assert r["nsec"] == 1 and r["sec_type"] == [W.E_MINUS]
+            assert r["sec"][0]["e"] == np.float32(e)
+    # low energy in lead: photoelectric dominates
+    r = oracle.step_one(oworld, W.GAMMA, _photon(oworld, 0.02, id=1))
+    assert r["proc"] == oracle.PROC_PHOT
+
+
+def test_annihilation_at_rest(oworld):
+    # a 0.5 MeV positron ranges out in one step (loss limit), then annihilates at rest
+    for i in range(200):
+        tr = _photon(oworld, 0.5, nia=50.0, id=i)
+        r = oracle.step_one(oworld, W.E_PLUS, tr)
+        assert r["lim"] == oracle.LIM_LOSS and r["death"] == oracle.DEATH_CUT
+        assert r["nsec"] == 2 and r["sec_type"] == [W.GAMMA, W.GAMMA]
+        a, b = r["sec"]
+        assert a["e"] == b["e"] == np.float32(MC2)
+        da = np.array([a["dx"], a["dy"], a["dz"]])
+        db = np.array([b["dx"], b["dy"], b["dz"]])
+        assert np.array_equal(da, -db)
+        assert np.linalg.norm(da) == pytest.approx(1.0, abs=1e-6)
+        assert r["mcr"] == 2 * float(np.float32(MC2))
+        assert r["dep_cont"] == float(np.float32(0.5))    # the whole kinetic energy
+
+
+def test_geometry_limits(oworld):
+    # photon along +z from the front face: stops exactly on the first plane, enters slab 1
+    tr = oracle.make_track(z=0.0, d=(0.0, 0.0, 1.0), e=1.0, nia=1e6, slab=0)
+    r = oracle.step_one(oworld, W.GAMMA, tr)
+    t = r["track"]
+    assert r["lim"] == oracle.LIM_Z and t["z"] == np.float32(2.3) and t["slab"] == 1
+    assert t["len"] == np.float32(2.3)
+    assert t["time"] == np.float32(np.float32(2.3) / np.float32(299.792458))
+    # backwards out of slab 0: escapes with its energy
+    tr = oracle.make_track(z=1.0, d=(0.0, 0.0, -1.0), e=3.0, nia=1e6, slab=0)
+    r = oracle.step_one(oworld, W.GAMMA, tr)
+    assert r["death"] == oracle.DEATH_ESCAPE and r["esc"] == 3.0
+    # sideways through the +x face
+    tr = oracle.make_track(x=199.0, z=1.0, d=(1.0, 0.0, 0.0), e=3.0, nia=1e6, slab=0)
+    r = oracle.step_one(oworld, W.GAMMA, tr)
+    assert r["lim"] == oracle.LIM_X and r["death"] == oracle.DEATH_ESCAPE
+    assert r["track"]["x"] == np.float32(200.0)
+    # a 100 MeV electron in lead takes the 20% energy-loss step
+    tr = oracle.make_track(z=0.1, d=(0.6, 0.0, 0.8), e=100.0, nia=1e6, slab=0)
+    r = oracle.step_one(oworld, W.E_MINUS, tr)
+    s = np.float32(np.float32(0.2) * np.float32(100.0)) / np.float32(1.274)
+    # the z plane at 2.3 mm is reached after 2.75 mm, the loss limit at 15.7 mm
+    assert r["lim"] == oracle.LIM_Z
+    tr = oracle.make_track(z=0.1, d=(0.0, 0.0, 1.0), e=100.0, nia=1e6, slab=0)
+    wide = oracle.World(W.single_slab(1000.0), oworld.tables, seed=1)
+    r = oracle.step_one(wide, W.E_MINUS, tr)
+    assert r["lim"] == oracle.LIM_LOSS and r["track"]["len"] == s
+
+
+def test_range_closed_form(otables):
+    # brems switched off: an electron loses T0 continuously over the range T0/dEdx
+    t = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in otables.items()}
+    t["sig32"][:, oracle.TAB_BREM] = 0
+    t["sig64"][:, oracle.TAB_BREM] = 0
+    w = oracle.World(W.single_slab(5000.0, material=0), t, seed=1)
+    t0 = 50.0
+    tr = oracle.make_track(z=0.0, e=t0, slab=0)
+    dep, n = 0.0, 0
+    while True:
+        r = oracle.step_one(w, W.E_MINUS, tr)
+        dep += r["dep_cont"] + r["cut"]
+        n += 1
+        if not r["alive"]:
+            break
+        tr = np.array([r["track"]], dtype=oracle.TRACK32_DTYPE)
+    assert dep == pytest.approx(t0, rel=1e-12)
+    assert float(r["track"]["len"]) == pytest.approx(t0 / float(np.float32(1.274)), rel=1e-5)
+    assert n == 19    # 18 steps of 20% loss (50 * 0.8^18 < 1 MeV) and the range-out step
+
+
+def test_attenuation_unscattered_fraction(otables):
+    e, L, n = 1.0, 10.0, 20000
+    geom = W.single_slab(L, material=0)
+    p = W.gun(n, e, ptype=W.GAMMA)
+    r = oracle.run(geom, p, seed=4, idlog=True, tables=otables)
+    log = r["idlog"]
+    prim = (log["id"] & np.uint64(0xFFFFFFFF)) == 0
+    death = log["type_death"] >> 8
+    through = prim & (log["steps"] == 1) & (death == oracle.DEATH_ESCAPE)
+    frac = through.sum() / n
+    sig = sum(oracle.sigma(k, 0, e) for k in ("compton", "pair", "phot"))
+    pexp = np.exp(-sig * L)
+    assert abs(frac - pexp) < 4 * np.sqrt(pexp * (1 - pexp) / n) + 1e-3
+
+
+def _ledger_rel(r):
+    L = r["ledger"]
+    src = L[:, 0] + L[:, 4]
+    snk = L[:, 1] + L[:, 2] + L[:, 3] + L[:, 5]
+    return np.max(np.abs(src - snk) / src)
+
+
+def test_run_invariants_small_electrons(geom, otables):
+    p = W.small_electrons()
+    r = oracle.run(geom, p, seed=1, idlog=True, tables=otables)
+    assert _ledger_rel(r) < 1e-12
+    L = r["ledger"]
+    assert np.allclose(r["score"].sum(1), L[:, 1] + L[:, 2], rtol=1e-12, atol=0)
+    assert np.all(L[:, 0] == 1000.0)
+    c = r["counts"].astype(np.int64)
+    assert list(c[0]) == [16, 0, 0]
+    assert c.sum() == int(r["steps"].sum())
+    assert np.array_equal(c.sum(0), r["steps"].astype(np.int64))
+    log = r["idlog"]
+    assert len(log) == int(r["tracks"].sum())
+    assert len(np.unique(log["id"])) == len(log)
+    assert int(log["steps"].astype(np.int64).sum()) == int(r["steps"].sum())
+    assert np.array_equal(np.bincount(log["type_death"] & 0xFF, minlength=3),
+                          r["tracks"].astype(np.int64))
+    # a 1 GeV shower in 22 X0 deposits nearly all its energy
+    assert 0.95 < (r["score"].sum(1) / L[:, 0]).mean() <= 1.0
+
+
+def test_run_invariants_mixed_types(geom, otables):
+    p = W.mixed_primaries(60)
+    p["ekin"] = np.minimum(p["ekin"], np.float32(3000.0))
+    r = oracle.run(geom, p, seed=1, idlog=True, tables=otables, nthreads=4)
+    assert _ledger_rel(r) < 1e-12
+    L = r["ledger"]
+    assert np.all(L[:, 4] > 0)        # every event annihilates positrons
+    r1 = oracle.run(geom, p, seed=1, idlog=True, tables=otables, nthreads=1)
+    assert np.array_equal(r["score"], r1["score"])
+    assert np.array_equal(r["counts"], r1["counts"])
+    assert np.array_equal(np.sort(r["idlog"], order="id"), np.sort(r1["idlog"], order="id"))
+
+
+def test_fp64_reference_agrees_with_strict(geom, otables):
+    p = W.gun(300, 1000.0)
+    a = oracle.run(geom, p, seed=1, tables=otables, nthreads=4)
+    b = oracle.run(geom, p, seed=1, tables=otables, nthreads=4, mode=oracle.REF_FP64)
+    assert _ledger_rel(b) < 1e-12
+    la = a["score"].reshape(300, 50, 2).sum(2)
+    lb = b["score"].reshape(300, 50, 2).sum(2)
+    diff = la - lb
+    se = np.sqrt(la.var(0) / 300 + lb.var(0) / 300) + 1e-12
+    assert np.all(np.abs(diff.mean(0)) <= 3 * se + 1e-9)
+    tot_a, tot_b = la.sum(0), lb.sum(0)
+    big = tot_a > 0.01 * tot_a.sum()
+    assert np.all(np.abs(tot_a[big] - tot_b[big]) / tot_a[big] < 0.01)
+
+
+@pytest.mark.parametrize("e", [0.013, 0.05, 0.3, 1.7, 25.0, 900.0, 4.2e4])
+def test_transport_sees_tabulated_cross_section(otables, e):
+    # with nia = 1 the physics step is 1/Sigma(E): the lookup (log, index, fraction,
+    # linear interpolation) must reproduce the closed form to the interpolation error
+    w = oracle.World(W.single_slab(1e9, material=0), otables, seed=1)
+    tr = oracle.make_track(z=0.0, e=e, nia=1.0, slab=0)
+    r = oracle.step_one(w, W.GAMMA, tr)
+    assert r["lim"] == oracle.LIM_PHYS
+    sig = sum(oracle.sigma(k, 0, e) for k in ("compton", "pair", "phot"))
+    # linear interpolation in ln E over bins of h = ln(1e8)/256: for the E^-3 photoelectric
+    # term the error is below (3h)^2/8 = 0.58%; the other terms are much flatter
+    f_pe = oracle.sigma("phot", 0, e) / sig
+    assert float(r["track"]["len"]) == pytest.approx(1.0 / sig, rel=0.006 * f_pe + 1e-3)
+    if e > 0.02:
+        tr = oracle.make_track(z=0.0, e=e, nia=1e-3, slab=0)
+        r = oracle.step_one(w, W.E_MINUS, tr)
+        assert r["lim"] == oracle.LIM_PHYS
+        assert float(r["track"]["len"]) == pytest.approx(1e-3 / oracle.sigma("brem", 0, e), rel=2e-3)
+
+
+def test_deposits_land_in_the_traversed_and_final_slabs(oworld):
+    # a 15 keV electron 5 um before the lead/argon plane: the step ends on the plane
+    # (geometry limit), the electron drops below the cut there; the continuous loss
+    # belongs to the slab it crossed, the remainder to the slab it ended in
+    z = np.float32(2.3) - np.float32(0.005)
+    n_seen = 0
+    for i in range(50):
+        tr = oracle.make_track(z=float(z), d=(0.0, 0.0, 1.0), e=0.015, nia=1e6, slab=0, id=i)
+        r = oracle.step_one(oworld, W.E_MINUS, tr)
+        assert r["lim"] == oracle.LIM_Z and r["track"]["slab"] == 1
+        assert r["death"] == oracle.DEATH_CUT
+        assert r["slab_cont"] == 0 and r["slab_cut"] == 1
+        assert r["dep_cont"] + r["cut"] == pytest.approx(0.015, rel=1e-6)
+        n_seen += 1
+    assert n_seen == 50
+
+
+def test_interaction_lengths_carry_across_boundaries(oworld):
+    # fraction of 1 MeV photons crossing one full layer (2.3 mm Pb + 5.7 mm lAr)
+    # without interacting is exp(-(S_Pb 2.3 + S_Ar 5.7)) with S the total cross sections
+    e, n, survived = 1.0, 20000, 0
+    for i in range(n):
+        tr = oracle.make_track(z=0.0, e=e, nia=-1.0, slab=0, id=i)
+        while True:
+            r = oracle.step_one(oworld, W.GAMMA, tr)
+            if r["lim"] == oracle.LIM_PHYS:
+                break
+            if r["track"]["slab"] == 2:
+                survived += 1
+                break
+            tr = np.array([r["track"]], dtype=oracle.TRACK32_DTYPE)
+    s = [sum(oracle.sigma(k, m, e) for k in ("compton", "pair", "phot")) for m in (0, 1)]
+    p = np.exp(-(s[0] * 2.3 + s[1] * 5.7))
+    assert abs(survived / n - p) < 4 * np.sqrt(p * (1 - p) / n) + 1e-3
+
+
+def test_charged_time_of_flight(oworld):
+    t = 0.3
+    tr = oracle.make_track(z=0.0, d=(0.0, 0.0, 1.0), e=t, nia=1e6, slab=0)
+    r = oracle.step_one(oworld, W.E_MINUS, tr)
+    s = float(r["track"]["len"])
+    beta = np.sqrt(1.0 - (MC2 / (t + MC2)) ** 2)
+    assert float(r["track"]["time"]) == pytest.approx(s / (beta * 299.792458), rel=1e-5)
