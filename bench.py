@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark of the EM shower transport hot path (one JSON line on rank 0).
+
+A step is one complete transport run of the workload (reset, inject, iterate until no
+track is left): 1,000 electrons of 10 GeV with 1 mrad direction jitter into the 50-layer
+Pb/lAr calorimeter (92.1 M track-steps, 263 iterations), in the tuned form (dense double
+buffer, AoSoA-32, persistent kernel, strict FP32 with FP64 scoring).  Reported:
+
+  value         track-steps/s, primaries resident in device memory, L2 flushed between steps
+  e2e           the same through the C ABI with host buffers (H2D of the primaries and D2H
+                of the scores inside each timed step)
+  roofline      the transport kernel against the HBM roofline: algorithmic bytes per launch
+                (64 B read per step + 64 B per survivor + 64 B per secondary = 64 (2 S - P))
+                over its CUDA-event duration, against the measured copy bandwidth
+  plain         the plain form (sparse single buffer, AoS, host loop) on the same workload
+  cpu_baseline  the CPU oracle on the host cores
+
+--impl reference times the CPU oracle (the reference arm of this build).  Under torchrun
+each rank runs its own replica of the workload (independent events: weak scaling); the
+time is the max over ranks and the value the steps of all ranks over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "track-steps/s and HBM GB/s (frac of peak), tuned vs plain; p99 event latency"
+UNIT = "track-steps/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="jittered", choices=["jittered", "small", "mixed"])
+    ap.add_argument("--form", default="dense", choices=["dense", "sparse"])
+    ap.add_argument("--layout", default="aosoa32", choices=["aos", "soa", "aosoa32", "aosoa64"])
+    ap.add_argument("--driver", default="persistent", choices=["hostloop", "graph", "persistent"])
+    ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
+    ap.add_argument("--block-size", type=int, default=256)
+    ap.add_argument("--capacity-log2", type=int, default=22)
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed plumbing
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    group = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        group = dist
+    return rank, world, local, group
+
+
+def barrier(group):
+    if group is not None:
+        group.barrier()
+
+
+def aggregate(local_steps: float, local_seconds: float, group):
+    """Whole-job steps (sum over ranks) and time (max over ranks)."""
+    if group is None:
+        return local_steps, local_seconds
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and group.get_backend() == "nccl" else "cpu"
+    s = torch.tensor([local_steps], dtype=torch.float64, device=dev)
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    group.all_reduce(s, op=group.ReduceOp.SUM)
+    group.all_reduce(t, op=group.ReduceOp.MAX)
+    return float(s.item()), float(t.item())
+
+
+# ------------------------------------------------------------------ inputs
+
+def make_workload(name: str, rank: int):
+    from paper_2302_08252_gb300 import workloads as W
+    if name == "jittered":
+        p = W.jittered_electrons(seed=W.PRIMARY_SEED + rank)
+        desc = "1000 e- 10 GeV, 1 mrad jitter, 50x(2.3 mm Pb + 5.7 mm lAr)"
+    elif name == "small":
+        p = W.small_electrons()
+        desc = "16 e- 1 GeV on +z, 50x(2.3 mm Pb + 5.7 mm lAr)"
+    else:
+        p = W.mixed_primaries(10000, seed=W.PRIMARY_SEED + rank)
+        desc = "10000 mixed e-/e+/gamma 0.1-100 GeV, 1 cm2 spot, 50x(2.3 mm Pb + 5.7 mm lAr)"
+    n_events = int(p["event"].max()) + 1
+    return W.calorimeter(), p, n_events, desc
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the run (timestamps kept to select the timed window)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "50"]
+        if device_id:
+            cmd += ["-i", device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return []
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                    frac = float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    rows.append({"t": ts + frac, "sm": float(parts[1]), "sm_max": float(parts[2]),
+                                 "power": parts[3], "active": parts[4], "hw": parts[5],
+                                 "hw_thermal": parts[6], "sw_thermal": parts[7],
+                                 "sw_power": parts[8]})
+                except (ValueError, IndexError):
+                    continue
+        os.unlink(self.out.name)
+        return rows
+
+
+def summarize_clocks(rows, t0, t1):
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+    inside = [r for r in rows if t0 - 0.05 <= r["t"] <= t1 + 0.05] or rows
+    reasons = set()
+    for r in inside:
+        for key, name in (("hw", "hw_slowdown"), ("hw_thermal", "hw_thermal_slowdown"),
+                          ("sw_thermal", "sw_thermal_slowdown"), ("sw_power", "sw_power_cap")):
+            if r[key].lower().startswith("active"):
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(r["sm"] for r in inside),
+            "sm_max_mhz": max(r["sm_max"] for r in inside), "reasons": sorted(reasons),
+            "samples": len(inside)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def algorithmic_bytes(steps: int, primaries: int) -> int:
+    """64 B read per step, 64 B per survivor (steps - deaths), 64 B per secondary; every
+    track dies once, so deaths = primaries + secondaries and the sum is 64 (2 S - P)."""
+    return 64 * (2 * steps - primaries)
+
+
+def committed_traffic(kernel_key: str):
+    """DRAM bytes per track-step of the transport kernel from the committed ncu summary,
+    only while the library sources are the ones it was measured on."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        from paper_2302_08252_gb300 import build
+        if d.get("fingerprint") != build._fingerprint():
+            return None
+        return d.get("kernels", {}).get(kernel_key)
+    except (OSError, ValueError):
+        return None
+
+
+def run_config(et, geom, prim, n_events, args, form, layout, driver, steps, warmup, flush,
+               timing=True):
+    import torch
+    # the sparse form never reuses a slot: it needs room for every track of the run
+    cap = args.capacity_log2 if form == "dense" else max(args.capacity_log2, 24)
+    ctx = et.make_context(geom, max_events=n_events, capacity_log2=cap,
+                          form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
+                          layout=layout, driver=driver,
+                          mode=et.MODE_STRICT if args.mode == "strict" else et.MODE_FAST,
+                          block_size=args.block_size, seed=1)
+    d_prim = torch.from_numpy(prim.view(np.uint8).copy()).cuda()
+    n = len(prim)
+    stream = torch.cuda.current_stream()
+
+    def one():
+        et.et_reset(ctx)
+        et.et_inject_device(ctx, d_prim, n)
+        return et.et_run_until_empty(ctx)
+
+    for _ in range(warmup):
+        one()
+    et.et_set_timing(ctx, timing)
+    et.et_read_timing(ctx)
+    ms_steps, tot_steps, launches, iters = [], 0, 0, 0
+    for _ in range(steps):
+        flush.add_(1)  # write > L2 between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tot = one()
+        b.record(stream)
+        b.synchronize()
+        ms_steps.append(a.elapsed_time(b))
+        tot_steps += tot["steps"]
+        iters += tot["iterations"]
+        launches += et.et_read_counters(ctx)["kernel_launches"]
+    kms, klaunch = et.et_read_timing(ctx)
+    return {"ctx": ctx, "ms": ms_steps, "steps": tot_steps, "launches": launches,
+            "kernel_ms": kms, "kernel_launches": klaunch, "iterations": iters, "n_prim": n}
+
+
+def e2e_measure(et, ctx, prim, n_events, n_slabs, steps):
+    import torch
+    torch.cuda.synchronize()
+    secs, tot = 0.0, 0
+    h2d = prim.nbytes
+    d2h = n_events * n_slabs * 8 + n_events * 5 * 8
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        et.et_reset(ctx)
+        et.et_inject(ctx, prim)
+        r = et.et_run_until_empty(ctx)
+        et.et_read_scoring_all(ctx, n_events, n_slabs)
+        secs += time.perf_counter() - t0
+        tot += r["steps"]
+    return tot, secs, h2d, d2h
+
+
+def cpu_baseline(geom, prim, n_events):
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = oracle.run(geom, prim, n_events=n_events, seed=1, nthreads=cores)
+    dt = time.perf_counter() - t0
+    steps = int(r["steps"].sum())
+    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"whole workload ({len(prim)} primaries, {steps} steps) on {cores} threads,"
+                      f" {dt:.2f} s wall"}
+
+
+# ------------------------------------------------------------------ arms
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2302_08252_gb300 import workloads as W
+    geom, prim, n_events, desc = make_workload(args.workload, 0)
+    events = list(range(min(n_events, 100)))
+    sample = W.select_events(prim, events)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
+    secs, steps = 0.0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
+        secs += time.perf_counter() - t0
+        steps += int(r["steps"].sum())
+    value = steps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "sample_events": len(events), "mode": "strict",
+                   "implementation": "CPU oracle (plain C, depth-first per event)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {len(events)} events per step on {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_arm(args, rank, world, group):
+    import torch
+
+    from paper_2302_08252_gb300 import et
+    dev = torch.cuda.current_device()
+    geom, prim, n_events, desc = make_workload(args.workload, rank)
+    n_slabs = len(geom["thickness"])
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = None if args.no_clocks else ClockSampler(uuid)
+
+    barrier(group)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    tuned = run_config(et, geom, prim, n_events, args, args.form, args.layout, args.driver,
+                       args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(group)
+    clock_rows = sampler.stop() if sampler else []
+
+    secs = sum(tuned["ms"]) / 1e3
+    all_steps, max_secs = aggregate(float(tuned["steps"]), secs, group)
+    value = all_steps / max_secs
+    steps_per_run = tuned["steps"] // args.steps
+
+    peak, peak_kind = measured_hbm_peak()
+    alg_per_launch = None
+    achieved = None
+    if tuned["kernel_launches"]:
+        per_launch_ms = tuned["kernel_ms"] / tuned["kernel_launches"]
+        # with the persistent driver one launch is one run; otherwise bytes are split evenly
+        runs_per_launch = args.steps / tuned["kernel_launches"]
+        alg_per_launch = algorithmic_bytes(steps_per_run, tuned["n_prim"]) * runs_per_launch
+        achieved = alg_per_launch / (per_launch_ms / 1e3) / 1e9
+    key = f"{args.mode}/{args.form}/{args.layout}/{args.driver}"
+    tr = committed_traffic(key)
+    traffic = tr * steps_per_run * (args.steps / max(1, tuned["kernel_launches"])) if tr else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_secs * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": desc, "form": args.form, "layout": args.layout,
+                   "driver": args.driver, "mode": args.mode, "block_size": args.block_size,
+                   "steps_per_run": steps_per_run,
+                   "iterations_per_run": tuned["iterations"] // args.steps,
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "hbm_gbs_alg_whole_step": algorithmic_bytes(steps_per_run, tuned["n_prim"]) /
+        (secs / args.steps) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "kernel": f"transport kernel ({key})",
+                     "alg_bytes_per_launch": alg_per_launch},
+        "gpu_launches": tuned["launches"],
+    }
+
+    barrier(group)
+    e2e_steps, e2e_secs, h2d, d2h = e2e_measure(et, tuned["ctx"], prim, n_events, n_slabs,
+                                                args.e2e_steps)
+    e2e_all, e2e_max = aggregate(float(e2e_steps), e2e_secs, group)
+    line["e2e"] = {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}
+    if rank == 0 and world == 1:
+        if not args.no_plain:
+            plain = run_config(et, geom, prim, n_events, args, "sparse", "aos", "hostloop",
+                               args.plain_steps, 1, flush, timing=False)
+            pv = plain["steps"] / (sum(plain["ms"]) / 1e3)
+            line["plain"] = {"value": pv, "unit": UNIT, "form": "sparse", "layout": "aos",
+                             "driver": "hostloop", "steps": args.plain_steps}
+            line["tuned_vs_plain"] = value / pv
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events)
+    line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local, group = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return reference_arm(args, rank, world)
+        return ours_arm(args, rank, world, group)
+    finally:
+        if group is not None:
+            group.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * et.h -- C ABI of the GB300 EM shower transport hot path.
+ *
+ * One transport iteration advances every active track of every particle type
+ * (e-, e+, gamma) by one step; survivors and secondaries become the tracks of
+ * the next iteration (paper Sec. 2).  The tracks live per type either in a
+ * "dense double buffer" (two dense arrays, current and next, filled by
+ * compaction, Sec. 2 / Fig. 1b) or in a "sparse single buffer" (one sparse
+ * array plus two slot lists, Sec. 2 / Fig. 1a), in one of the layouts of
+ * Sec. 4 (AoS, SoA, AoSoA-32, AoSoA-64), optionally instrumented to count
+ * per-field reads/writes and per-word accesses (Sec. 5).  The benchmark shape
+ * (an electron gun into 50 absorber/gap layers, energy scored per layer) is
+ * that of Sec. 4; the physics is a fixed toy EM model.
+ *
+ * Conventions
+ *  - Every function returns et_status; nothing aborts and nothing throws.
+ *    After a failure, et_last_error(ctx) describes it.
+ *  - Host pointers passed in are read during the call only (the library copies
+ *    what it keeps); the caller keeps ownership.  Output pointers are host
+ *    memory the caller owns, unless a name says "_device".
+ *  - The library owns all device memory of a context.  It allocates through the
+ *    caller's allocator callbacks when given (e.g. a framework's caching
+ *    allocator), else with cudaMalloc.  All work is issued on cfg.cuda_stream
+ *    (NULL: the legacy default stream).
+ *  - A context is used from one host thread at a time.
+ *  - Calls out of order (inject before tables, etc.) return ET_ERR_STATE.
+ *  - Device-side failures (a full track buffer, a bounded wait that ran out)
+ *    are recorded in a device status word and reported by the next call that
+ *    synchronises (et_run_iteration, et_run_until_empty, et_read_*).
+ */
+#ifndef ET_H
+#define ET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct et_ctx et_ctx;
+
+typedef enum {
+  ET_OK = 0,
+  ET_ERR_INVALID = 1,   /* bad argument */
+  ET_ERR_CAPACITY = 2,  /* a track buffer, event table or log is full */
+  ET_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  ET_ERR_TIMEOUT = 4,   /* a bounded device wait ran out (persistent driver) */
+  ET_ERR_STATE = 5,     /* call out of order */
+  ET_ERR_NOMEM = 6      /* allocation failed */
+} et_status;
+
+enum { ET_EMINUS = 0, ET_EPLUS = 1, ET_GAMMA = 2, ET_NTYPES = 3 };
+enum { ET_FORM_SPARSE = 0, ET_FORM_DENSE = 1 };
+enum { ET_LAYOUT_AOS = 0, ET_LAYOUT_SOA = 1, ET_LAYOUT_AOSOA32 = 2, ET_LAYOUT_AOSOA64 = 3 };
+enum { ET_MODE_STRICT = 0, ET_MODE_FAST = 1 };
+enum { ET_DRIVER_HOSTLOOP = 0, ET_DRIVER_GRAPH = 1, ET_DRIVER_PERSISTENT = 2 };
+
+/* Device allocator callbacks: return NULL on failure. */
+typedef void* (*et_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*et_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  uint32_t capacity_log2;   /* track slots per type and buffer (dense) or per type (sparse) */
+  int32_t form;             /* ET_FORM_* */
+  int32_t layout;           /* ET_LAYOUT_* */
+  int32_t mode;             /* ET_MODE_*: strict = bit-exact toy model, fast = intrinsics + FMA */
+  int32_t driver;           /* ET_DRIVER_*: how et_run_until_empty iterates */
+  int32_t block_size;       /* threads per block of the step kernels (64..1024, multiple of 32; 0 = 256) */
+  uint64_t seed;            /* physics seed: Philox key word 0 is its low 32 bits */
+  uint32_t max_events;      /* events are numbered 0..max_events-1 */
+  uint32_t max_iters;       /* length of the per-iteration count log */
+  int32_t instrument;       /* 1: count per-field reads/writes and per-word accesses */
+  int32_t id_log;           /* 1: record (id, steps, type|death<<8) of every track at its death */
+  uint64_t id_log_capacity; /* records (when id_log) */
+  void* cuda_stream;        /* cudaStream_t */
+  et_alloc_fn alloc;        /* optional; both or neither */
+  et_free_fn free;
+  void* alloc_user;
+} et_config;
+
+/* Create a context (allocates the track buffers).  *out is NULL on failure. */
+et_status et_create(const et_config* cfg, et_ctx** out);
+et_status et_destroy(et_ctx* ctx);
+const char* et_last_error(const et_ctx* ctx);
+
+/*
+ * Calorimeter geometry (paper Sec. 4: 50 alternating absorber/gap box layers).
+ * n_slabs (<= 128) slabs stacked along +z from z = 0; thickness_mm[n_slabs]
+ * (FP64; the plane positions are the FP64 running sums rounded to FP32);
+ * material[n_slabs] indexes the tables (< n_materials); |x|, |y| <= half_xy_mm.
+ * Outside is vacuum: a track leaving the box escapes.
+ */
+et_status et_create_geometry(et_ctx* ctx, uint32_t n_slabs, const double* thickness_mm,
+                             const uint8_t* material, float half_xy_mm);
+
+/*
+ * Cross-section tables of the toy model, per material m < n_materials (<= 4):
+ * sigma[m][k][i] (1/mm) for k = 0 Compton, 1 pair, 2 photoelectric, 3 photon
+ * total, 4 bremsstrahlung, at nodes i < n_nodes (257) spaced uniformly in
+ * ln E; a lookup takes x = (log E - log_emin) * inv_dlog.  dedx[m] in MeV/mm.
+ * The lookup constants are FP32 values (the strict model fixes them).
+ * Tables are staged in shared memory by every step kernel (8 KB per material).
+ */
+et_status et_load_tables(et_ctx* ctx, uint32_t n_materials, uint32_t n_nodes, float log_emin,
+                         float inv_dlog, const float* sigma, const float* dedx);
+
+/*
+ * The toy model's own tables, computed on the host from the FP64 closed forms
+ * and rounded to FP32 (Compton: Klein-Nishina; pair: log rise above 2 mc^2;
+ * photoelectric: Z^4/E^3; brems: ln(T/k_c)/X0), for materials 0 = lead and
+ * 1 = liquid argon.  sigma_out[n_materials][5][n_nodes], dedx_out[n_materials].
+ */
+et_status et_build_toy_tables(uint32_t n_materials, uint32_t n_nodes, float* sigma_out,
+                              float* dedx_out, float* log_emin_out, float* inv_dlog_out);
+
+/* A primary particle (48 bytes). */
+typedef struct {
+  uint32_t type;   /* ET_EMINUS, ET_EPLUS, ET_GAMMA */
+  uint32_t event;  /* < max_events */
+  uint64_t id;     /* unique; convention (event << 32) | index in event */
+  float pos[3];    /* mm, inside the calorimeter */
+  float dir[3];    /* unit vector */
+  float ekin;      /* MeV (kinetic; photon energy) */
+  uint32_t pad;
+} et_primary;
+
+/*
+ * Inject n primaries (host array, copied): they become active tracks of the
+ * next iteration.  Their injected energy is added to their events' ledgers.
+ */
+et_status et_inject(et_ctx* ctx, const et_primary* primaries, size_t n);
+
+/*
+ * As et_inject, for primaries already in device memory (n records of
+ * et_primary, 16-byte aligned, read by a kernel on the context's stream; the
+ * caller keeps them alive until that stream passes this point).  Each record
+ * is validated on the device; an invalid one is skipped and reported as
+ * ET_ERR_INVALID by the next synchronising call.
+ */
+et_status et_inject_device(et_ctx* ctx, const et_primary* primaries_device, size_t n);
+
+typedef struct {
+  uint32_t n_active[3];     /* tracks per type active in the next iteration */
+  uint32_t pad;
+  uint64_t steps;           /* track steps taken (this iteration / in total) */
+  uint64_t secondaries;     /* secondaries created */
+} et_iter_stats;
+
+/* One transport iteration (always host-driven; stats may be NULL). */
+et_status et_run_iteration(et_ctx* ctx, et_iter_stats* out);
+
+/*
+ * Iterate until no track is left or max_iters more iterations ran, with the
+ * configured driver (host loop, CUDA graph, persistent kernel).  Totals and
+ * the number of iterations run are optional outputs.
+ */
+et_status et_run_until_empty(et_ctx* ctx, uint64_t max_iters, et_iter_stats* totals,
+                             uint64_t* n_iters);
+
+/* Energy ledger of one event (MeV). */
+typedef struct {
+  double injected, deposited_cont, below_cut, escaped, mass_created, mass_consumed;
+} et_ledger;
+
+/* Per-slab deposits (continuous + below-cut, FP64) and the ledger of one event. */
+et_status et_read_scoring(et_ctx* ctx, uint32_t event, double* slab_dep, size_t n_slabs,
+                          et_ledger* out);
+
+/* All events at once: score[max_events][n_slabs], ledger[max_events] (either may be NULL). */
+et_status et_read_scoring_all(et_ctx* ctx, double* score, et_ledger* ledger);
+
+/* Tracks stepped per iteration and type since the last reset: counts[n][3], n <= cap. */
+et_status et_read_iteration_counts(et_ctx* ctx, uint64_t* counts, uint64_t cap, uint64_t* n);
+
+/* Death records (16 bytes each: id, steps, type | death << 8); needs cfg.id_log. */
+typedef struct {
+  uint64_t id;
+  uint32_t steps;
+  uint32_t type_death;
+} et_idrec;
+et_status et_read_id_log(et_ctx* ctx, et_idrec* out, uint64_t cap, uint64_t* n);
+
+/* Instrumented build (cfg.instrument): reads/writes per type and field,
+ * counts[3][15][2] over the 15 leaf fields of the 64-byte track record. */
+et_status et_read_field_trace(et_ctx* ctx, uint64_t* counts);
+
+/* Instrumented build: accesses per 4-byte word of one track buffer (type, half
+ * 0/1; the sparse form has half 0 only); out[capacity * 16] uint32. */
+et_status et_read_heatmap(et_ctx* ctx, uint32_t type, uint32_t half, uint32_t* out, uint64_t cap);
+
+/* Run counters (host copies). */
+typedef struct {
+  uint64_t steps[3];          /* per type */
+  uint64_t secondaries[3];    /* per type */
+  uint64_t iterations;        /* since reset */
+  uint64_t slot_high_water[3];/* sparse: slots ever used; dense: peak next-buffer fill */
+  uint64_t reject_cap_hits;   /* Compton sampler attempt cap reached */
+  uint64_t kernel_launches;   /* launches issued by the library since reset */
+  uint32_t status;            /* device status word (0 = fine) */
+  uint32_t pad;
+} et_counters;
+et_status et_read_counters(et_ctx* ctx, et_counters* out);
+
+/* Forget all tracks, scores, ledgers, logs and counters (buffers stay allocated). */
+et_status et_reset(et_ctx* ctx);
+
+/*
+ * Timing of the step kernels (CUDA events on the context's stream around every
+ * step-kernel launch, or around the persistent kernel): total milliseconds and
+ * number of timed launches since the last call.  Enabled by et_set_timing(ctx, 1).
+ */
+et_status et_set_timing(et_ctx* ctx, int on);
+et_status et_read_timing(et_ctx* ctx, double* ms_total, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

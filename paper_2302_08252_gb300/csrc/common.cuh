@@ -1,0 +1,231 @@
+// Shared definitions of the GPU transport path: track record, device control
+// block, kernel arguments, Philox4x32-10, track ids and the strict-mode
+// elementary functions of the toy model.
+//
+// Track record (64 bytes, 15 leaf fields): the stand-in for AdePT's track
+// struct of the paper's Sec. 3 (position, navigation state, ...), here
+// position, direction, kinetic energy, interaction lengths left, id, event,
+// track-local step, slab (the navigation state), and three cold fields (time,
+// track length, flags) so that the instrumentation sees hot and cold fields
+// as the paper's heatmaps do (Sec. 5).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace et {
+
+enum { EM = 0, EP = 1, GAM = 2, NTYPES = 3 };
+enum { LIM_Z = 0, LIM_X = 1, LIM_Y = 2, LIM_LOSS = 3, LIM_PHYS = 4 };
+enum { PROC_NONE = 0, PROC_COMPTON = 1, PROC_PAIR = 2, PROC_PHOT = 3, PROC_BREM = 4 };
+enum { ALIVE = 0, DEATH_ESCAPE = 1, DEATH_CUT = 2, DEATH_ABSORB = 3 };
+enum { MODE_STRICT = 0, MODE_FAST = 1 };
+
+// device status bits
+enum : uint32_t {
+  ST_CAPACITY = 1u,       // a next buffer / slot pool overflowed (writes were dropped)
+  ST_TIMEOUT = 2u,        // grid barrier wait ran out
+  ST_LOG_FULL = 4u,       // id log full (records dropped)
+  ST_ITER_LOG_FULL = 8u,  // iteration count log full
+  ST_BAD_PRIMARY = 16u,   // a device-side primary failed validation (skipped)
+};
+
+// ---- leaf fields of the track record: byte offset and size ----
+enum Leaf {
+  F_X = 0, F_Y, F_Z, F_DX, F_DY, F_DZ, F_E, F_NIA, F_ID, F_EVENT, F_STEP, F_SLAB, F_TIME, F_LEN,
+  F_FLAGS, NLEAF
+};
+__host__ __device__ constexpr int leaf_off(int f) { return f <= F_NIA ? 4 * f : (f == F_ID ? 32 : 4 * f + 4); }
+__host__ __device__ constexpr int leaf_size(int f) { return f == F_ID ? 8 : 4; }
+static_assert(leaf_off(F_FLAGS) == 60, "record is 64 bytes");
+static_assert(leaf_off(F_EVENT) == 40, "id is 8 bytes at 32");
+
+struct Trk {
+  float x, y, z, dx, dy, dz, e, nia;
+  uint64_t id;
+  uint32_t event, step;
+  int32_t slab;
+  float time, len;
+  uint32_t flags;
+};
+
+// dirty-leaf bits for the sparse form's in-place update
+enum : uint32_t {
+  D_POS = (1u << F_X) | (1u << F_Y) | (1u << F_Z),
+  D_DIR = (1u << F_DX) | (1u << F_DY) | (1u << F_DZ),
+  D_E = 1u << F_E,
+  D_NIA = 1u << F_NIA,
+  D_STEP = 1u << F_STEP,
+  D_SLAB = 1u << F_SLAB,
+  D_TIME = 1u << F_TIME,
+  D_LEN = 1u << F_LEN,
+  D_FLAGS = 1u << F_FLAGS,
+  D_ALL = (1u << NLEAF) - 1u,
+};
+
+// ---- device control block (one per context) ----
+struct DevCtl {
+  uint32_t cnt[3][NTYPES];      // tracks per type; slot it%3 = current, (it+1)%3 = next
+  uint32_t iter;                // iteration about to run
+  uint32_t status;              // ST_* bits
+  uint32_t done;                // 1 when no track is left (graph driver)
+  uint32_t stop_iter;           // the graph/persistent drivers stop before this iteration
+  unsigned long long secondaries[NTYPES];
+  unsigned long long steps[NTYPES];
+  unsigned long long reject_cap_hits;
+  unsigned long long idlog_n;
+  uint32_t hwm[NTYPES];         // sparse: slots handed out; dense: peak next fill
+  uint32_t bar_count;           // grid barrier (persistent driver)
+  uint32_t bar_gen;
+  uint32_t free_top[NTYPES];    // sparse free-slot stacks (serving)
+  uint32_t status_snap;         // status as seen by the last grid barrier
+  uint32_t pad;
+};
+
+struct IdRec {
+  unsigned long long id;
+  uint32_t steps;
+  uint32_t type_death;
+};
+
+// ---- kernel arguments (passed by value) ----
+struct Args {
+  char* trk[NTYPES][2];         // dense: [type][half]; sparse: [type][0]
+  uint32_t* idx[NTYPES][2];     // sparse: slot lists [type][parity]
+  uint32_t* freelist[NTYPES];   // sparse: free-slot stacks (NULL: slots are never reused)
+  uint32_t cap;                 // slots per buffer
+  DevCtl* ctl;
+  uint32_t* counts_log;         // [max_iters][3]
+  uint32_t max_iters;
+  uint32_t n_slabs;
+  double* score;                // [max_events][n_slabs]
+  double* ledger;               // [max_events][5]: injected, cut, escaped, mass_created, mass_consumed
+  uint32_t max_events;
+  uint32_t n_mat;
+  const float4* tab_cp;         // [n_mat][256] {C, C[i+1]-C[i], P, P[i+1]-P[i]}
+  const float2* tab_tot;        // [n_mat][256] {T, dT}
+  const float2* tab_brem;       // [n_mat][256] {B, dB}
+  const float* planes;          // [n_slabs + 1]
+  const uint8_t* mat;           // [n_slabs]
+  float half_xy, log_emin, inv_dlog;
+  float dedx[4];
+  uint32_t seed_lo;
+  IdRec* idlog;                 // NULL: off
+  unsigned long long idlog_cap;
+  unsigned long long* trace;    // [3][15][2] or NULL
+  uint32_t* heat[NTYPES][2];    // per-word access counts or NULL
+  unsigned long long timeout_ns;// bounded waits (persistent driver)
+};
+
+constexpr int MAX_SLABS = 128;
+constexpr int MAX_MAT = 4;
+constexpr int NBINS = 256;  // table intervals (257 nodes)
+
+// ---- Philox4x32-10 (Salmon et al., SC'11), written from its published definition ----
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// (x >> 8) + 1 is at most 2^24, so both the conversion and the scaling are exact.
+__device__ __forceinline__ float u01(uint32_t x) {
+  return (float)((x >> 8) + 1u) * 0x1p-24f;
+}
+
+// SplitMix64 finalizer (Steele, Lea, Flood, OOPSLA 2014)
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint64_t secondary_id(uint64_t parent, uint32_t step,
+                                                          uint32_t ordinal) {
+  const uint64_t tag = ((uint64_t)step << 2) | (uint64_t)(ordinal & 3u) | (1ull << 62);
+  return mix64(parent ^ mix64(tag));
+}
+
+// ---- strict-mode elementary functions of the toy model ----
+// log: x = m 2^e, m in (sqrt(1/2), sqrt(2)], log m = 2 atanh((m-1)/(m+1)) to r^9, e ln2 as hi+lo
+// (Cody-Waite).  exp: n = rint(x/ln2), r = (x - n ln2_hi) - n ln2_lo, Taylor degree 7, 2^n by
+// exponent bits.  sincos(2 pi u): 4u = q + y, |y| <= 1/2, a = y pi/2, Taylor sin to a^9 and
+// cos to a^8, rotated by the quadrant q.  These translation units are built with --fmad=false.
+__device__ __forceinline__ float s_log(float x) {
+  const uint32_t b = __float_as_uint(x);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+  if (m > 0x1.6a09e6p+0f) {
+    m = m * 0.5f;
+    e = e + 1;
+  }
+  const float r = (m - 1.0f) / (m + 1.0f);
+  const float r2 = r * r;
+  float s = 0x1.c71c72p-4f;           // 1/9
+  s = s * r2 + 0x1.24924ap-3f;        // 1/7
+  s = s * r2 + 0x1.99999ap-3f;        // 1/5
+  s = s * r2 + 0x1.555556p-2f;        // 1/3
+  s = s * r2;
+  const float t = r + r * s;
+  const float lm = t + t;
+  const float fe = (float)e;
+  return fe * 0x1.62e4p-1f + (lm + fe * 0x1.7f7d1cp-20f);
+}
+
+__device__ __forceinline__ float s_exp(float x) {
+  if (x > 88.0f) return __uint_as_float(0x7f800000u);
+  if (x < -87.0f) return 0.0f;
+  const float n = rintf(x * 0x1.715476p+0f);
+  float r = x - n * 0x1.62e4p-1f;
+  r = r - n * 0x1.7f7d1cp-20f;
+  float p = 0x1.a01a02p-13f;          // 1/5040
+  p = p * r + 0x1.6c16c2p-10f;        // 1/720
+  p = p * r + 0x1.111112p-7f;         // 1/120
+  p = p * r + 0x1.555556p-5f;         // 1/24
+  p = p * r + 0x1.555556p-3f;         // 1/6
+  p = p * r + 0.5f;
+  p = p * r + 1.0f;
+  p = p * r + 1.0f;
+  const int ni = (int)n;
+  return p * __uint_as_float((uint32_t)(ni + 127) << 23);
+}
+
+__device__ __forceinline__ void s_sincos2pi(float u, float* so, float* co) {
+  const float v = 4.0f * u;
+  const float q = rintf(v);
+  const float y = v - q;
+  const float a = y * 0x1.921fb6p+0f;
+  const float a2 = a * a;
+  float ps = 0x1.71de3ap-19f;         // 1/9!
+  ps = ps * a2 - 0x1.a01a02p-13f;     // 1/7!
+  ps = ps * a2 + 0x1.111112p-7f;      // 1/5!
+  ps = ps * a2 - 0x1.555556p-3f;      // 1/3!
+  ps = ps * a2 + 1.0f;
+  const float sa = a * ps;
+  float pc = 0x1.a01a02p-16f;         // 1/8!
+  pc = pc * a2 - 0x1.6c16c2p-10f;     // 1/6!
+  pc = pc * a2 + 0x1.555556p-5f;      // 1/4!
+  pc = pc * a2 - 0.5f;
+  pc = pc * a2 + 1.0f;
+  const float ca = pc;
+  const int k = ((int)q) & 3;
+  if (k == 0) { *so = sa; *co = ca; }
+  else if (k == 1) { *so = ca; *co = -sa; }
+  else if (k == 2) { *so = -sa; *co = -ca; }
+  else { *so = -ca; *co = sa; }
+}
+
+}  // namespace et

@@ -1,0 +1,732 @@
+// Host side of the C ABI declared in include/et.h: context and device-memory
+// management, geometry and table upload, injection, the three iteration
+// drivers (host loop, CUDA graph with a device-side WHILE condition,
+// persistent cooperative kernel) and the read-back calls.
+//
+// The iteration is the paper's transport iteration (Sec. 2): all active tracks
+// of all types take one step; the device control block keeps the per-type
+// counts triple-buffered (current / next / recycled) so that no host round
+// trip is needed between iterations except in the host-loop driver, which
+// mirrors the plain AdePT loop (launch per type, read counts back).
+#define ET_HOST_TU
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "et.h"
+#include "kernels.cuh"
+#include "registry.h"
+
+using namespace et;
+
+static_assert(sizeof(et_primary) == 48, "primary record is 48 bytes");
+static_assert(sizeof(Primary) == 48, "device primary record is 48 bytes");
+static_assert(sizeof(et_idrec) == sizeof(IdRec), "id record layout");
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+struct et_ctx {
+  et_config cfg{};
+  std::string err;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  uint32_t cap = 0;
+  bool dense = true;
+  std::vector<void*> allocs;
+  KernelSet ks{};
+  Args args{};
+  DevCtl* d_ctl = nullptr;
+  DevCtl* h_ctl = nullptr;  // pinned
+  uint32_t* h_stop = nullptr;  // pinned scratch for stop_iter uploads
+  bool have_geom = false, have_tables = false;
+  std::vector<float> planes;
+  std::vector<uint8_t> mat;
+  Primary* d_stage = nullptr;
+  size_t stage_cap = 0;
+  int block = 256;
+  int grid_fixed[3] = {0, 0, 0};  // step kernels in the graph driver (grid-stride)
+  int grid_persistent = 0;
+  size_t smem_g = 0, smem_e = 0, smem_all = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool timing = false;
+  std::vector<EventPair> evpool;
+  size_t ev_used = 0;
+  double ms_acc = 0.0;
+  uint64_t timed = 0;
+  uint64_t launches = 0;
+  int fault_skip_block = -1;  // fault injection for the persistent driver's barrier (tests)
+};
+
+static et_status fail(et_ctx* c, et_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CUDA_TRY(c, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail((c), ET_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static void* dalloc(et_ctx* c, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->cfg.cuda_stream, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+static void register_kernels(int mode, int layout, KernelSet* ks) {
+  static void (*const fns[2][4])(KernelSet*) = {
+      {et_register_kernels_0_0, et_register_kernels_0_1, et_register_kernels_0_2,
+       et_register_kernels_0_3},
+      {et_register_kernels_1_0, et_register_kernels_1_1, et_register_kernels_1_2,
+       et_register_kernels_1_3}};
+  fns[mode][layout](ks);
+}
+
+// ---- timing of step-kernel launches ----
+static EventPair* timing_begin(et_ctx* c) {
+  if (!c->timing) return nullptr;
+  if (c->ev_used == c->evpool.size()) {
+    EventPair p;
+    if (cudaEventCreate(&p.a) != cudaSuccess || cudaEventCreate(&p.b) != cudaSuccess) return nullptr;
+    c->evpool.push_back(p);
+  }
+  EventPair* p = &c->evpool[c->ev_used++];
+  cudaEventRecord(p->a, c->stream);
+  return p;
+}
+static void timing_end(et_ctx* c, EventPair* p) {
+  if (p) cudaEventRecord(p->b, c->stream);
+}
+// after a stream synchronize: accumulate and recycle the events
+static void timing_collect(et_ctx* c) {
+  for (size_t i = 0; i < c->ev_used; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->evpool[i].a, c->evpool[i].b) == cudaSuccess) {
+      c->ms_acc += ms;
+      c->timed += 1;
+    }
+  }
+  c->ev_used = 0;
+}
+
+static et_status sync_ctl(et_ctx* c) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  timing_collect(c);
+  const uint32_t st = c->h_ctl->status;
+  if (st & ST_TIMEOUT) return fail(c, ET_ERR_TIMEOUT, "device wait timed out (status 0x%x)", st);
+  if (st & ST_CAPACITY)
+    return fail(c, ET_ERR_CAPACITY, "track buffer capacity %u exceeded (status 0x%x)", c->cap, st);
+  if (st & ST_LOG_FULL) return fail(c, ET_ERR_CAPACITY, "id log full (status 0x%x)", st);
+  if (st & ST_BAD_PRIMARY) return fail(c, ET_ERR_INVALID, "invalid device-side primary (skipped)");
+  if (st & ST_ITER_LOG_FULL)
+    return fail(c, ET_ERR_CAPACITY, "iteration log full (max_iters %u)", c->cfg.max_iters);
+  return ET_OK;
+}
+
+static et_status launch(et_ctx* c, const void* fn, int grid, int block, size_t smem, void** params) {
+  CUDA_TRY(c, cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, c->stream));
+  c->launches += 1;
+  return ET_OK;
+}
+
+extern "C" {
+
+const char* et_last_error(const et_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+et_status et_create(const et_config* cfg, et_ctx** out) {
+  if (!out) return ET_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg) return ET_ERR_INVALID;
+  et_config k = *cfg;
+  if (k.block_size == 0) k.block_size = 256;
+  if (k.max_iters == 0) k.max_iters = 1u << 16;
+  if (k.capacity_log2 < 6 || k.capacity_log2 > 28 || (k.form != 0 && k.form != 1) ||
+      k.layout < 0 || k.layout > 3 || (k.mode != 0 && k.mode != 1) || k.driver < 0 ||
+      k.driver > 2 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
+      k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) ||
+      ((k.alloc == nullptr) != (k.free == nullptr)))
+    return ET_ERR_INVALID;
+  et_ctx* c = new et_ctx();
+  c->cfg = k;
+  c->stream = (cudaStream_t)k.cuda_stream;
+  c->cap = 1u << k.capacity_log2;
+  c->dense = k.form == ET_FORM_DENSE;
+  c->block = k.block_size;
+  *out = c;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(c, ET_ERR_CUDA, "no CUDA device");
+  }
+  register_kernels(k.mode, k.layout, &c->ks);
+
+  Args& a = c->args;
+  const size_t rec = (size_t)c->cap * 64u;
+  for (int t = 0; t < 3; ++t) {
+    for (int h = 0; h < (c->dense ? 2 : 1); ++h) {
+      a.trk[t][h] = (char*)dalloc(c, rec);
+      if (!a.trk[t][h]) return fail(c, ET_ERR_NOMEM, "track buffer of %zu bytes", rec);
+    }
+    if (!c->dense) {
+      for (int h = 0; h < 2; ++h) {
+        a.idx[t][h] = (uint32_t*)dalloc(c, (size_t)c->cap * 4u);
+        if (!a.idx[t][h]) return fail(c, ET_ERR_NOMEM, "slot list");
+      }
+    }
+    if (k.instrument) {
+      for (int h = 0; h < (c->dense ? 2 : 1); ++h) {
+        a.heat[t][h] = (uint32_t*)dalloc(c, (size_t)c->cap * 16u * 4u);
+        if (!a.heat[t][h]) return fail(c, ET_ERR_NOMEM, "heatmap");
+      }
+    }
+  }
+  a.cap = c->cap;
+  a.ctl = c->d_ctl = (DevCtl*)dalloc(c, sizeof(DevCtl));
+  a.counts_log = (uint32_t*)dalloc(c, (size_t)k.max_iters * 3u * 4u);
+  a.max_iters = k.max_iters;
+  a.max_events = k.max_events;
+  a.ledger = (double*)dalloc(c, (size_t)k.max_events * 5u * 8u);
+  if (!a.ctl || !a.counts_log || !a.ledger) return fail(c, ET_ERR_NOMEM, "control block");
+  if (k.instrument) {
+    a.trace = (unsigned long long*)dalloc(c, 3u * NLEAF * 2u * 8u);
+    if (!a.trace) return fail(c, ET_ERR_NOMEM, "trace");
+  }
+  if (k.id_log) {
+    if (k.id_log_capacity == 0) return fail(c, ET_ERR_INVALID, "id_log needs id_log_capacity");
+    a.idlog = (IdRec*)dalloc(c, (size_t)k.id_log_capacity * sizeof(IdRec));
+    if (!a.idlog) return fail(c, ET_ERR_NOMEM, "id log");
+    a.idlog_cap = k.id_log_capacity;
+  }
+  a.seed_lo = (uint32_t)k.seed;
+  a.timeout_ns = 2000000000ull;
+  if (cudaMallocHost(&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
+      cudaMallocHost(&c->h_stop, 64) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(c, ET_ERR_NOMEM, "pinned host memory");
+  }
+  return et_reset(c);
+}
+
+et_status et_destroy(et_ctx* c) {
+  if (!c) return ET_ERR_INVALID;
+  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  for (auto& p : c->evpool) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (void* p : c->allocs) {
+    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
+    else cudaFree(p);
+  }
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->h_stop) cudaFreeHost(c->h_stop);
+  (void)cudaGetLastError();
+  delete c;
+  return ET_OK;
+}
+
+et_status et_reset(et_ctx* c) {
+  if (!c) return ET_ERR_INVALID;
+  Args& a = c->args;
+  CUDA_TRY(c, cudaMemsetAsync(a.ctl, 0, sizeof(DevCtl), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(a.counts_log, 0, (size_t)a.max_iters * 3u * 4u, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(a.ledger, 0, (size_t)a.max_events * 5u * 8u, c->stream));
+  if (a.score)
+    CUDA_TRY(c, cudaMemsetAsync(a.score, 0, (size_t)a.max_events * a.n_slabs * 8u, c->stream));
+  if (a.trace) CUDA_TRY(c, cudaMemsetAsync(a.trace, 0, 3u * NLEAF * 2u * 8u, c->stream));
+  for (int t = 0; t < 3; ++t)
+    for (int h = 0; h < 2; ++h)
+      if (a.heat[t][h])
+        CUDA_TRY(c, cudaMemsetAsync(a.heat[t][h], 0, (size_t)c->cap * 64u, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->launches = 0;
+  c->ev_used = 0;
+  c->ms_acc = 0.0;
+  c->timed = 0;
+  memset(c->h_ctl, 0, sizeof(DevCtl));
+  return ET_OK;
+}
+
+et_status et_create_geometry(et_ctx* c, uint32_t n_slabs, const double* thickness_mm,
+                             const uint8_t* material, float half_xy_mm) {
+  if (!c) return ET_ERR_INVALID;
+  if (c->have_geom) return fail(c, ET_ERR_STATE, "geometry already set");
+  if (n_slabs < 1 || n_slabs > (uint32_t)MAX_SLABS || !thickness_mm || !material ||
+      !(half_xy_mm > 0.0f) || !std::isfinite(half_xy_mm))
+    return fail(c, ET_ERR_INVALID, "bad geometry arguments");
+  std::vector<float> planes(n_slabs + 1);
+  std::vector<uint8_t> mat(n_slabs);
+  double z = 0.0;
+  planes[0] = 0.0f;
+  for (uint32_t s = 0; s < n_slabs; ++s) {
+    if (!(thickness_mm[s] > 0.0) || !std::isfinite(thickness_mm[s]) || material[s] >= MAX_MAT)
+      return fail(c, ET_ERR_INVALID, "bad slab %u", s);
+    z = z + thickness_mm[s];  // FP64 running sum, rounded once
+    planes[s + 1] = (float)z;
+    mat[s] = material[s];
+  }
+  Args& a = c->args;
+  float* dp = (float*)dalloc(c, planes.size() * 4);
+  uint8_t* dm = (uint8_t*)dalloc(c, 128);
+  double* sc = (double*)dalloc(c, (size_t)a.max_events * n_slabs * 8u);
+  if (!dp || !dm || !sc) return fail(c, ET_ERR_NOMEM, "geometry");
+  CUDA_TRY(c, cudaMemcpyAsync(dp, planes.data(), planes.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(dm, mat.data(), n_slabs, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(sc, 0, (size_t)a.max_events * n_slabs * 8u, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  a.planes = dp;
+  a.mat = dm;
+  a.score = sc;
+  a.n_slabs = n_slabs;
+  a.half_xy = half_xy_mm;
+  c->planes = planes;
+  c->mat = mat;
+  c->have_geom = true;
+  return ET_OK;
+}
+
+et_status et_load_tables(et_ctx* c, uint32_t n_materials, uint32_t n_nodes, float log_emin,
+                         float inv_dlog, const float* sigma, const float* dedx) {
+  if (!c) return ET_ERR_INVALID;
+  if (c->have_tables) return fail(c, ET_ERR_STATE, "tables already loaded");
+  if (n_materials < 1 || n_materials > (uint32_t)MAX_MAT || n_nodes != NBINS + 1 || !sigma ||
+      !dedx || !std::isfinite(log_emin) || !(inv_dlog > 0.0f))
+    return fail(c, ET_ERR_INVALID, "tables: need 1..4 materials and 257 nodes");
+  const size_t nb = (size_t)n_materials * NBINS;
+  std::vector<float2> tot(nb), brem(nb);
+  std::vector<float4> cp(nb);
+  for (uint32_t m = 0; m < n_materials; ++m) {
+    if (!(dedx[m] > 0.0f) || !std::isfinite(dedx[m])) return fail(c, ET_ERR_INVALID, "dedx");
+    const float* T = sigma + (size_t)m * 5 * n_nodes;
+    for (uint32_t q = 0; q < 5 * n_nodes; ++q)
+      if (!std::isfinite(T[q]) || T[q] < 0.0f) return fail(c, ET_ERR_INVALID, "table value");
+    for (int i = 0; i < NBINS; ++i) {
+      const float* C = T + 0 * n_nodes;
+      const float* P = T + 1 * n_nodes;
+      const float* S = T + 3 * n_nodes;
+      const float* B = T + 4 * n_nodes;
+      // {value at node i, FP32 difference to node i+1}: the interpolation
+      // T[i] + f (T[i+1] - T[i]) is then one multiply and one add
+      tot[m * NBINS + i] = make_float2(S[i], S[i + 1] - S[i]);
+      cp[m * NBINS + i] = make_float4(C[i], C[i + 1] - C[i], P[i], P[i + 1] - P[i]);
+      brem[m * NBINS + i] = make_float2(B[i], B[i + 1] - B[i]);
+    }
+    c->args.dedx[m] = dedx[m];
+  }
+  Args& a = c->args;
+  float2* dt = (float2*)dalloc(c, nb * 8);
+  float2* db = (float2*)dalloc(c, nb * 8);
+  float4* dc = (float4*)dalloc(c, nb * 16);
+  if (!dt || !db || !dc) return fail(c, ET_ERR_NOMEM, "tables");
+  CUDA_TRY(c, cudaMemcpyAsync(dt, tot.data(), nb * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(db, brem.data(), nb * 8, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(dc, cp.data(), nb * 16, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  a.tab_tot = dt;
+  a.tab_brem = db;
+  a.tab_cp = dc;
+  a.n_mat = n_materials;
+  a.log_emin = log_emin;
+  a.inv_dlog = inv_dlog;
+  c->smem_all = smem_bytes((int)n_materials);
+  c->smem_g = c->smem_all;
+  c->smem_e = c->smem_all;
+  // grids: grid-stride kernels sized to fill the machine
+  int occ = 0;
+  for (int t = 0; t < 3; ++t) {
+    const void* fn = c->ks.step[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0][t];
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->block, c->smem_all));
+    c->grid_fixed[t] = (occ > 0 ? occ : 1) * c->num_sms;
+  }
+  const void* pf = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pf, c->block, c->smem_all));
+  if (occ < 1) return fail(c, ET_ERR_CUDA, "persistent kernel does not fit on an SM");
+  c->grid_persistent = occ * c->num_sms;
+  c->have_tables = true;
+  return ET_OK;
+}
+
+et_status et_inject(et_ctx* c, const et_primary* p, size_t n) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (n == 0) return ET_OK;
+  if (!p || n > c->cap) return fail(c, ET_ERR_INVALID, "bad primaries");
+  const float h = c->args.half_xy;
+  const uint32_t ns = c->args.n_slabs;
+  for (uint32_t s = 0; s < ns; ++s)
+    if (c->mat[s] >= c->args.n_mat)
+      return fail(c, ET_ERR_STATE, "slab %u uses material %u but %u tables are loaded", s,
+                  (unsigned)c->mat[s], c->args.n_mat);
+  for (size_t i = 0; i < n; ++i) {
+    const et_primary& q = p[i];
+    const bool ok = q.type < 3 && q.event < c->cfg.max_events && q.ekin > 0.0f &&
+                    std::isfinite(q.ekin) && std::fabs(q.pos[0]) <= h && std::fabs(q.pos[1]) <= h &&
+                    q.pos[2] >= c->planes[0] && q.pos[2] < c->planes[ns] &&
+                    std::isfinite(q.dir[0]) && std::isfinite(q.dir[1]) && std::isfinite(q.dir[2]);
+    if (!ok) return fail(c, ET_ERR_INVALID, "primary %zu is invalid", i);
+  }
+  if (n > c->stage_cap) {
+    c->d_stage = (Primary*)dalloc(c, n * sizeof(Primary));
+    if (!c->d_stage) return fail(c, ET_ERR_NOMEM, "primary staging");
+    c->stage_cap = n;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, p, n * sizeof(Primary), cudaMemcpyHostToDevice, c->stream));
+  uint32_t nn = (uint32_t)n;
+  const Primary* dp = c->d_stage;
+  void* params[] = {(void*)&c->args, (void*)&dp, (void*)&nn};
+  const int grid = (int)((n + 255) / 256);
+  return launch(c, c->ks.inject[c->dense ? 1 : 0], grid, 256, 0, params);
+}
+
+et_status et_inject_device(et_ctx* c, const et_primary* p, size_t n) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (n == 0) return ET_OK;
+  if (!p || n > c->cap || ((uintptr_t)p & 15u) != 0) return fail(c, ET_ERR_INVALID, "bad primaries");
+  for (uint32_t s = 0; s < c->args.n_slabs; ++s)
+    if (c->mat[s] >= c->args.n_mat) return fail(c, ET_ERR_STATE, "slab material without table");
+  uint32_t nn = (uint32_t)n;
+  const Primary* dp = reinterpret_cast<const Primary*>(p);
+  void* params[] = {(void*)&c->args, (void*)&dp, (void*)&nn};
+  return launch(c, c->ks.inject[c->dense ? 1 : 0], (int)((n + 255) / 256), 256, 0, params);
+}
+
+// Launch the three step kernels of one iteration; counts from the last read-back.
+static et_status launch_step_kernels(et_ctx* c, const uint32_t n[3], bool fixed_grid) {
+  void* params[] = {(void*)&c->args};
+  const int instr = c->cfg.instrument ? 1 : 0, dn = c->dense ? 1 : 0;
+  for (int t = 0; t < 3; ++t) {
+    if (!fixed_grid && n[t] == 0) continue;
+    int grid = fixed_grid ? c->grid_fixed[t] : (int)((n[t] + c->block - 1) / c->block);
+    if (grid > c->grid_fixed[t]) grid = c->grid_fixed[t];
+    if (grid < 1) grid = 1;
+    EventPair* ev = fixed_grid ? nullptr : timing_begin(c);
+    et_status s = launch(c, c->ks.step[instr][dn][t], grid, c->block, c->smem_all, params);
+    timing_end(c, ev);
+    if (s != ET_OK) return s;
+  }
+  return ET_OK;
+}
+
+static et_status launch_end(et_ctx* c, cudaGraphConditionalHandle h, int use) {
+  void* params[] = {(void*)&c->args, (void*)&h, (void*)&use};
+  return launch(c, (const void*)k_end_iteration, 1, 1, 0, params);
+}
+
+static et_status one_hostloop_iteration(et_ctx* c, bool* empty) {
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const uint32_t it = c->h_ctl->iter;
+  const uint32_t* n = c->h_ctl->cnt[it % 3];
+  *empty = (n[0] + n[1] + n[2]) == 0;
+  if (*empty) return ET_OK;
+  if (it >= c->cfg.max_iters) return fail(c, ET_ERR_CAPACITY, "iteration log full");
+  c->h_stop[0] = 0xffffffffu;
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
+  s = launch_step_kernels(c, n, false);
+  if (s != ET_OK) return s;
+  return launch_end(c, 0, 0);
+}
+
+static void fill_stats(et_ctx* c, const DevCtl& before, et_iter_stats* out) {
+  if (!out) return;
+  const DevCtl& now = *c->h_ctl;
+  const uint32_t cur = now.iter % 3;
+  for (int t = 0; t < 3; ++t) out->n_active[t] = now.cnt[cur][t];
+  out->pad = 0;
+  out->steps = 0;
+  out->secondaries = 0;
+  for (int t = 0; t < 3; ++t) {
+    out->steps += now.steps[t] - before.steps[t];
+    out->secondaries += now.secondaries[t] - before.secondaries[t];
+  }
+}
+
+et_status et_run_iteration(et_ctx* c, et_iter_stats* out) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const DevCtl before = *c->h_ctl;
+  bool empty = false;
+  s = one_hostloop_iteration(c, &empty);
+  if (s != ET_OK) return s;
+  s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  fill_stats(c, before, out);
+  return ET_OK;
+}
+
+static et_status build_graph(et_ctx* c) {
+  cudaGraph_t g;
+  CUDA_TRY(c, cudaGraphCreate(&g, 0));
+  c->graph = g;
+  cudaGraphConditionalHandle h;
+  CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault));
+  // the params struct holds a union of node kinds: zero-filled storage, then the conditional part
+  alignas(cudaGraphNodeParams) unsigned char np_storage[sizeof(cudaGraphNodeParams)];
+  memset(np_storage, 0, sizeof np_storage);
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_storage);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CUDA_TRY(c, cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  CUDA_TRY(c, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = c->stream;
+  const uint64_t saved_launches = c->launches;
+  c->stream = cs;
+  et_status s = ET_OK;
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess) {
+    s = fail(c, ET_ERR_CUDA, "graph capture failed to start");
+  } else {
+    const uint32_t n[3] = {1, 1, 1};
+    s = launch_step_kernels(c, n, true);
+    if (s == ET_OK) s = launch_end(c, h, 1);
+    cudaGraph_t out_g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &out_g);
+    if (s == ET_OK && e != cudaSuccess)
+      s = fail(c, ET_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  c->stream = saved;
+  c->launches = saved_launches;
+  cudaStreamDestroy(cs);
+  if (s != ET_OK) return s;
+  CUDA_TRY(c, cudaGraphInstantiate(&c->gexec, g, 0));
+  return ET_OK;
+}
+
+et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* totals,
+                             uint64_t* n_iters) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const DevCtl before = *c->h_ctl;
+  const uint32_t it0 = before.iter;
+  const uint32_t* n0 = before.cnt[it0 % 3];
+  const bool empty0 = (n0[0] + n0[1] + n0[2]) == 0;
+  if (!empty0 && max_iters > 0) {
+    uint64_t lim = (uint64_t)it0 + max_iters;
+    if (lim > 0xffffffffull) lim = 0xffffffffull;
+    if (c->cfg.driver == ET_DRIVER_HOSTLOOP) {
+      for (uint64_t k = 0; k < max_iters; ++k) {
+        bool empty = false;
+        s = one_hostloop_iteration(c, &empty);
+        if (s != ET_OK) return s;
+        if (empty) break;
+      }
+    } else {
+      c->h_stop[0] = (uint32_t)lim;
+      CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
+      if (c->cfg.driver == ET_DRIVER_GRAPH) {
+        if (!c->gexec) {
+          s = build_graph(c);
+          if (s != ET_OK) return s;
+        }
+        EventPair* ev = timing_begin(c);
+        CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+        timing_end(c, ev);
+        c->launches += 1;
+      } else {
+        int fault = c->fault_skip_block;
+        void* params[] = {(void*)&c->args, (void*)&fault};
+        const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+        EventPair* ev = timing_begin(c);
+        CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block), params,
+                                                c->smem_all, c->stream));
+        timing_end(c, ev);
+        c->launches += 1;
+      }
+    }
+  }
+  s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  fill_stats(c, before, totals);
+  if (n_iters) *n_iters = c->h_ctl->iter - it0;
+  return ET_OK;
+}
+
+et_status et_read_scoring(et_ctx* c, uint32_t event, double* slab_dep, size_t n_slabs,
+                          et_ledger* out) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom) return fail(c, ET_ERR_STATE, "no geometry");
+  if (event >= c->cfg.max_events || (slab_dep && n_slabs < c->args.n_slabs))
+    return fail(c, ET_ERR_INVALID, "bad event or slab buffer");
+  std::vector<double> sc(c->args.n_slabs);
+  double lg[5];
+  CUDA_TRY(c, cudaMemcpyAsync(sc.data(), c->args.score + (size_t)event * c->args.n_slabs,
+                              sc.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(lg, c->args.ledger + (size_t)event * 5, sizeof lg,
+                              cudaMemcpyDeviceToHost, c->stream));
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  double sum = 0.0;
+  for (size_t i = 0; i < sc.size(); ++i) {
+    if (slab_dep) slab_dep[i] = sc[i];
+    sum += sc[i];
+  }
+  if (out) {
+    out->injected = lg[0];
+    out->below_cut = lg[1];
+    out->escaped = lg[2];
+    out->mass_created = lg[3];
+    out->mass_consumed = lg[4];
+    out->deposited_cont = sum - lg[1];
+  }
+  return ET_OK;
+}
+
+et_status et_read_scoring_all(et_ctx* c, double* score, et_ledger* ledger) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom) return fail(c, ET_ERR_STATE, "no geometry");
+  const size_t ne = c->cfg.max_events, ns = c->args.n_slabs;
+  std::vector<double> sc;
+  double* dst = score;
+  if (!dst && ledger) {
+    sc.resize(ne * ns);
+    dst = sc.data();
+  }
+  std::vector<double> lg(ledger ? ne * 5 : 0);
+  if (dst)
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->args.score, ne * ns * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (ledger)
+    CUDA_TRY(c, cudaMemcpyAsync(lg.data(), c->args.ledger, ne * 5 * 8, cudaMemcpyDeviceToHost, c->stream));
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  if (ledger) {
+    for (size_t e = 0; e < ne; ++e) {
+      double sum = 0.0;
+      for (size_t i = 0; i < ns; ++i) sum += dst[e * ns + i];
+      ledger[e].injected = lg[e * 5 + 0];
+      ledger[e].below_cut = lg[e * 5 + 1];
+      ledger[e].escaped = lg[e * 5 + 2];
+      ledger[e].mass_created = lg[e * 5 + 3];
+      ledger[e].mass_consumed = lg[e * 5 + 4];
+      ledger[e].deposited_cont = sum - lg[e * 5 + 1];
+    }
+  }
+  return ET_OK;
+}
+
+et_status et_read_iteration_counts(et_ctx* c, uint64_t* counts, uint64_t cap, uint64_t* n) {
+  if (!c || !n) return ET_ERR_INVALID;
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  uint64_t it = c->h_ctl->iter;
+  if (it > c->cfg.max_iters) it = c->cfg.max_iters;
+  *n = it;
+  if (!counts) return ET_OK;
+  if (cap < it) return fail(c, ET_ERR_CAPACITY, "count buffer too short (%llu < %llu)",
+                           (unsigned long long)cap, (unsigned long long)it);
+  std::vector<uint32_t> h(it * 3);
+  if (it)
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->args.counts_log, it * 12, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (uint64_t q = 0; q < it * 3; ++q) counts[q] = h[q];
+  return ET_OK;
+}
+
+et_status et_read_id_log(et_ctx* c, et_idrec* out, uint64_t cap, uint64_t* n) {
+  if (!c || !n) return ET_ERR_INVALID;
+  if (!c->args.idlog) return fail(c, ET_ERR_STATE, "id log not enabled");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  uint64_t m = c->h_ctl->idlog_n;
+  *n = m;
+  if (!out) return ET_OK;
+  if (cap < m) return fail(c, ET_ERR_CAPACITY, "id buffer too short");
+  if (m)
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->args.idlog, m * sizeof(IdRec), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return ET_OK;
+}
+
+et_status et_read_field_trace(et_ctx* c, uint64_t* counts) {
+  if (!c || !counts) return ET_ERR_INVALID;
+  if (!c->args.trace) return fail(c, ET_ERR_STATE, "not an instrumented context");
+  CUDA_TRY(c, cudaMemcpyAsync(counts, c->args.trace, 3u * NLEAF * 2u * 8u, cudaMemcpyDeviceToHost, c->stream));
+  return sync_ctl(c);
+}
+
+et_status et_read_heatmap(et_ctx* c, uint32_t type, uint32_t half, uint32_t* out, uint64_t cap) {
+  if (!c || !out || type > 2 || half > 1) return ET_ERR_INVALID;
+  if (!c->args.heat[type][half]) return fail(c, ET_ERR_STATE, "no heatmap for this buffer");
+  if (cap < (uint64_t)c->cap * 16u) return fail(c, ET_ERR_CAPACITY, "heatmap buffer too short");
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->args.heat[type][half], (size_t)c->cap * 64u, cudaMemcpyDeviceToHost, c->stream));
+  return sync_ctl(c);
+}
+
+et_status et_read_counters(et_ctx* c, et_counters* out) {
+  if (!c || !out) return ET_ERR_INVALID;
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  timing_collect(c);
+  const DevCtl& d = *c->h_ctl;
+  memset(out, 0, sizeof *out);
+  for (int t = 0; t < 3; ++t) {
+    out->steps[t] = d.steps[t];
+    out->secondaries[t] = d.secondaries[t];
+    out->slot_high_water[t] = d.hwm[t];
+  }
+  out->iterations = d.iter;
+  out->reject_cap_hits = d.reject_cap_hits;
+  out->kernel_launches = c->launches;
+  out->status = d.status;
+  return ET_OK;
+}
+
+et_status et_set_timing(et_ctx* c, int on) {
+  if (!c) return ET_ERR_INVALID;
+  c->timing = on != 0;
+  return ET_OK;
+}
+
+et_status et_read_timing(et_ctx* c, double* ms_total, uint64_t* launches) {
+  if (!c) return ET_ERR_INVALID;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  timing_collect(c);
+  if (ms_total) *ms_total = c->ms_acc;
+  if (launches) *launches = c->timed;
+  c->ms_acc = 0.0;
+  c->timed = 0;
+  return ET_OK;
+}
+
+// Test hooks (not in et.h): bounded-wait fault injection for the persistent driver.
+et_status et_debug_set_barrier_fault(et_ctx* c, int skip_block, uint64_t timeout_ns) {
+  if (!c) return ET_ERR_INVALID;
+  c->fault_skip_block = skip_block;
+  if (timeout_ns) c->args.timeout_ns = timeout_ns;
+  return ET_OK;
+}
+
+}  // extern "C"

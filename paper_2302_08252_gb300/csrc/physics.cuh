@@ -1,0 +1,355 @@
+// One step of one track of the toy EM model on the GPU (the per-track work
+// inside the paper's transport kernels, Sec. 2 and Sec. 4).  Strict mode
+// evaluates the model's fixed operation sequence in FP32 with the spec
+// polynomials (its translation units are built with --fmad=false, IEEE
+// division and square root), so results are bit-identical to the model's
+// definition; fast mode swaps in hardware intrinsics and allows FMA.
+//
+// Per step: Philox block 0 of (seed, event | id, step) -> interaction lengths,
+// cross section from the shared-memory tables, distances to the slab planes and
+// box faces, the step limiter in fixed order, move, continuous loss, boundary
+// crossing, then at most one discrete interaction (photon: Compton by
+// Butcher-Messel rejection, pair, photoelectric; e+-: bremsstrahlung with a 1/k
+// spectrum; positrons annihilate at rest below the cut).  The FP64 energy
+// balance of the step is the deposit.
+#pragma once
+
+#include "common.cuh"
+
+namespace et {
+
+constexpr float MC2 = 0x1.05a1a8p-1f;       // 0.51099895 MeV
+constexpr float TWO_MC2 = 0x1.05a1a8p+0f;   // 1.0219979 MeV
+constexpr float KC = 0x1.47ae14p-7f;        // 0.01 MeV, production and tracking cut
+constexpr float C_LIGHT = 0x1.2bcadep+8f;   // 299.792458 mm/ns
+constexpr float LOSS_FRAC = 0x1.99999ap-3f; // 0.2
+constexpr float F_INF = __builtin_huge_valf();
+
+// Shared-memory copy of geometry and tables (block-local).
+struct Tabs {
+  const float* planes;   // [n_slabs + 1]
+  const uint8_t* mat;    // [n_slabs]
+  const float2* tot;     // [n_mat][256] {Sigma_tot, next - this}
+  const float4* cp;      // [n_mat][256] {Sigma_C, dC, Sigma_pair, dP}
+  const float2* brem;    // [n_mat][256]
+  const float* dedx;     // [n_mat]
+  int n_slabs;
+};
+
+struct Sec {
+  float e, dx, dy, dz;
+  uint64_t id;
+  int type;
+};
+
+// At most 3 secondaries per step (brems photon + 2 annihilation photons; e- + 2
+// annihilation photons from a pair whose positron is below the cut).  They sit in
+// three named slots, never an indexed array, so that they stay in registers.
+struct StepOut {
+  int alive, death, nsec, reject, slab_cont;
+  uint32_t dirty;
+  Sec s0, s1, s2;
+  double dep, cut, esc, mc, mcr;
+  // k must be a compile-time constant after unrolling
+  __device__ __forceinline__ const Sec& sec(int k) const { return k == 0 ? s0 : (k == 1 ? s1 : s2); }
+};
+
+template <int MODE>
+__device__ __forceinline__ float m_log(float x) {
+  if constexpr (MODE == MODE_STRICT) return s_log(x);
+  else return __logf(x);
+}
+template <int MODE>
+__device__ __forceinline__ float m_exp(float x) {
+  if constexpr (MODE == MODE_STRICT) return s_exp(x);
+  else return __expf(x);
+}
+template <int MODE>
+__device__ __forceinline__ void m_sincos2pi(float u, float* s, float* c) {
+  if constexpr (MODE == MODE_STRICT) s_sincos2pi(u, s, c);
+  else __sincosf(6.28318530717958648f * u, s, c);
+}
+
+__device__ __forceinline__ void add_sec(StepOut& o, const Trk& t, uint32_t pstep, int type,
+                                        float e, float dx, float dy, float dz) {
+  const int k = o.nsec;
+  Sec s;
+  s.e = e;
+  s.dx = dx;
+  s.dy = dy;
+  s.dz = dz;
+  s.id = secondary_id(t.id, pstep, (uint32_t)k);
+  s.type = type;
+  if (k == 0) o.s0 = s;
+  else if (k == 1) o.s1 = s;
+  else o.s2 = s;
+  o.nsec = k + 1;
+}
+
+// direction at polar (cost, sint) and azimuth (cphi, sphi) about unit u
+__device__ __forceinline__ void rotate_about(float ux, float uy, float uz, float px, float py,
+                                             float pz, float& nx, float& ny, float& nz) {
+  float up = ux * ux + uy * uy;
+  if (up > 0.0f) {
+    up = sqrtf(up);
+    nx = (ux * uz * px - uy * py) / up + ux * pz;
+    ny = (uy * uz * px + ux * py) / up + uy * pz;
+    nz = uz * pz - up * px;
+  } else if (uz < 0.0f) {
+    nx = -px; ny = py; nz = -pz;
+  } else {
+    nx = px; ny = py; nz = pz;
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void annihilate(StepOut& o, const Trk& t, uint32_t pstep,
+                                           uint32_t seed) {
+  const uint4 r = philox((uint32_t)t.id, (uint32_t)(t.id >> 32), pstep, 65u, seed, t.event);
+  const float cost = 2.0f * u01(r.x) - 1.0f;
+  const float sint = sqrtf((1.0f - cost) * (1.0f + cost));
+  float sp, cp;
+  m_sincos2pi<MODE>(u01(r.y), &sp, &cp);
+  const float dx = sint * cp, dy = sint * sp, dz = cost;
+  add_sec(o, t, pstep, GAM, MC2, dx, dy, dz);
+  add_sec(o, t, pstep, GAM, MC2, -dx, -dy, -dz);
+  o.mcr = (double)MC2 + (double)MC2;
+}
+
+template <int TYPE, int MODE>
+__device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emin, float inv_dlog,
+                                           float half, uint32_t seed, StepOut& o) {
+  constexpr bool charged = TYPE != GAM;
+  o.alive = 1;
+  o.death = ALIVE;
+  o.nsec = 0;
+  o.reject = 0;
+  o.dep = o.cut = o.esc = o.mc = o.mcr = 0.0;
+  o.dirty = D_POS | D_NIA | D_STEP | D_TIME | D_LEN | D_FLAGS;
+  const uint32_t pstep = t.step;
+  const uint32_t idlo = (uint32_t)t.id, idhi = (uint32_t)(t.id >> 32);
+  const uint4 r0 = philox(idlo, idhi, pstep, 0u, seed, t.event);
+  const float E = t.e;
+
+  // interaction lengths left
+  if (t.nia < 0.0f) t.nia = -m_log<MODE>(u01(r0.x));
+
+  // cross section at the pre-step energy
+  const int s0 = t.slab;
+  const int m = tb.mat[s0];
+  const float lx = (m_log<MODE>(E) - log_emin) * inv_dlog;
+  int bin = (int)floorf(lx);
+  bin = bin < 0 ? 0 : bin;
+  bin = bin > NBINS - 1 ? NBINS - 1 : bin;
+  const float f = lx - (float)bin;
+  float sig;
+  if constexpr (charged) {
+    const float2 b = tb.brem[m * NBINS + bin];
+    sig = b.x + f * b.y;
+  } else {
+    const float2 b = tb.tot[m * NBINS + bin];
+    sig = b.x + f * b.y;
+  }
+  const float s_phys = (sig > 0.0f) ? t.nia / sig : F_INF;
+
+  // geometry: slab planes along z, box faces along x and y
+  float zpl = 0.0f, sz, sx, sy;
+  if (t.dz > 0.0f) { zpl = tb.planes[s0 + 1]; sz = (zpl - t.z) / t.dz; }
+  else if (t.dz < 0.0f) { zpl = tb.planes[s0]; sz = (zpl - t.z) / t.dz; }
+  else sz = F_INF;
+  if (sz < 0.0f) sz = 0.0f;
+  if (t.dx > 0.0f) sx = (half - t.x) / t.dx;
+  else if (t.dx < 0.0f) sx = (-half - t.x) / t.dx;
+  else sx = F_INF;
+  if (sx < 0.0f) sx = 0.0f;
+  if (t.dy > 0.0f) sy = (half - t.y) / t.dy;
+  else if (t.dy < 0.0f) sy = (-half - t.y) / t.dy;
+  else sy = F_INF;
+  if (sy < 0.0f) sy = 0.0f;
+
+  // step limiter: fixed order, earlier wins ties
+  float s = sz;
+  int lim = LIM_Z;
+  if (sx < s) { s = sx; lim = LIM_X; }
+  if (sy < s) { s = sy; lim = LIM_Y; }
+  float dedx = 0.0f;
+  if constexpr (charged) {
+    dedx = tb.dedx[m];
+    const float sl = (E > 1.0f) ? (LOSS_FRAC * E) / dedx : E / dedx;
+    if (sl < s) { s = sl; lim = LIM_LOSS; }
+  }
+  if (s_phys < s) { s = s_phys; lim = LIM_PHYS; }
+
+  // move
+  t.x = t.x + s * t.dx;
+  t.y = t.y + s * t.dy;
+  t.z = (lim == LIM_Z) ? zpl : (t.z + s * t.dz);
+  if constexpr (charged) {
+    const float beta = sqrtf(E * (E + TWO_MC2)) / (E + MC2);
+    t.time = t.time + s / (beta * C_LIGHT);
+  } else {
+    t.time = t.time + s / C_LIGHT;
+  }
+  t.len = t.len + s;
+  if (lim == LIM_PHYS) {
+    t.nia = -1.0f;
+  } else {
+    t.nia = t.nia - s * sig;
+    if (t.nia < 0.0f) t.nia = 0.0f;
+  }
+
+  // continuous loss, deposited in the pre-step slab
+  float eout = E;
+  if constexpr (charged) {
+    const float de = (lim == LIM_LOSS && E <= 1.0f) ? E : dedx * s;
+    eout = E - de;
+    if (eout < 0.0f) eout = 0.0f;
+    o.dirty |= D_E;
+  }
+  t.e = eout;
+  o.slab_cont = s0;
+
+  // boundary
+  bool escaped = false;
+  if (lim == LIM_Z) {
+    const int s1 = (t.dz > 0.0f) ? s0 + 1 : s0 - 1;
+    if (s1 < 0 || s1 >= tb.n_slabs) {
+      escaped = true;
+    } else {
+      t.slab = s1;
+      o.dirty |= D_SLAB;
+    }
+  } else if (lim == LIM_X || lim == LIM_Y) {
+    escaped = true;
+  }
+
+  int proc = PROC_NONE;
+  if (escaped) {
+    o.esc = (double)eout;
+    o.alive = 0;
+    o.death = DEATH_ESCAPE;
+  } else if (charged && eout < KC) {
+    o.cut = o.cut + (double)eout;
+    o.alive = 0;
+    o.death = DEATH_CUT;
+    if constexpr (TYPE == EP) annihilate<MODE>(o, t, pstep, seed);
+  } else if (lim == LIM_PHYS) {
+    if constexpr (!charged) {
+      const float4 cp = tb.cp[m * NBINS + bin];
+      const float sc = cp.x + f * cp.y;
+      const float sp = cp.z + f * cp.w;
+      const float r = u01(r0.y) * sig;
+      if (r < sc) {
+        // Compton (Butcher-Messel), attempt j on Philox block 1 + j, at most 64
+        proc = PROC_COMPTON;
+        const float k = E / MC2;
+        const float eps0 = 1.0f / (1.0f + 2.0f * k);
+        const float eps0sq = eps0 * eps0;
+        const float a1 = -m_log<MODE>(eps0);
+        const float a2 = 0.5f * (1.0f - eps0sq);
+        const float p1 = a1 / (a1 + a2);
+        float eps = 1.0f, epssq = 1.0f, onecost = 0.0f, sint2 = 0.0f;
+        int j;
+        for (j = 0; j < 64; ++j) {
+          const uint4 rj = philox(idlo, idhi, pstep, 1u + (uint32_t)j, seed, t.event);
+          const float ua = u01(rj.x), ub = u01(rj.y), uc = u01(rj.z);
+          if (p1 > ua) {
+            eps = m_exp<MODE>(-(a1 * ub));
+            epssq = eps * eps;
+          } else {
+            epssq = eps0sq + (1.0f - eps0sq) * ub;
+            eps = sqrtf(epssq);
+          }
+          onecost = (1.0f - eps) / (k * eps);
+          sint2 = onecost * (2.0f - onecost);
+          const float g = 1.0f - (eps * sint2) / (1.0f + epssq);
+          if (g >= uc) break;
+        }
+        if (j >= 64) o.reject = 1;
+        if (sint2 < 0.0f) sint2 = 0.0f;
+        const float cost = 1.0f - onecost;
+        const float sint = sqrtf(sint2);
+        float sphi, cphi;
+        m_sincos2pi<MODE>(u01(r0.w), &sphi, &cphi);
+        float nx, ny, nz;
+        rotate_about(t.dx, t.dy, t.dz, sint * cphi, sint * sphi, cost, nx, ny, nz);
+        const float e1 = eps * E;
+        const float te = E - e1;
+        if (te >= KC) {
+          const float px = E * t.dx - e1 * nx;
+          const float py = E * t.dy - e1 * ny;
+          const float pz = E * t.dz - e1 * nz;
+          const float pn = sqrtf(px * px + py * py + pz * pz);
+          add_sec(o, t, pstep, EM, te, px / pn, py / pn, pz / pn);
+        } else {
+          o.cut = o.cut + (double)te;
+        }
+        t.dx = nx;
+        t.dy = ny;
+        t.dz = nz;
+        t.e = e1;
+        o.dirty |= D_DIR | D_E;
+        if (!(e1 >= KC)) {
+          o.cut = o.cut + (double)e1;
+          o.alive = 0;
+          o.death = DEATH_CUT;
+        }
+      } else if (r < sc + sp && E > TWO_MC2) {
+        proc = PROC_PAIR;
+        const float avail = E - TWO_MC2;
+        const float em = u01(r0.z) * avail;
+        const float ep = avail - em;
+        o.mc = ((double)E - (double)em) - (double)ep;
+        if (em >= KC) add_sec(o, t, pstep, EM, em, t.dx, t.dy, t.dz);
+        else o.cut = o.cut + (double)em;
+        if (ep >= KC) {
+          add_sec(o, t, pstep, EP, ep, t.dx, t.dy, t.dz);
+        } else {
+          o.cut = o.cut + (double)ep;
+          annihilate<MODE>(o, t, pstep, seed);
+        }
+        o.alive = 0;
+        o.death = DEATH_ABSORB;
+      } else {
+        proc = PROC_PHOT;
+        if (E >= KC) add_sec(o, t, pstep, EM, E, t.dx, t.dy, t.dz);
+        else o.cut = o.cut + (double)E;
+        o.alive = 0;
+        o.death = DEATH_ABSORB;
+      }
+    } else {
+      proc = PROC_BREM;
+      if (eout > KC) {
+        float kk = KC * m_exp<MODE>(u01(r0.z) * m_log<MODE>(eout / KC));
+        if (kk < KC) kk = KC;
+        if (kk > eout) kk = eout;
+        add_sec(o, t, pstep, GAM, kk, t.dx, t.dy, t.dz);
+        const float t2 = eout - kk;
+        t.e = t2;
+        if (t2 < KC) {
+          o.cut = o.cut + (double)t2;
+          o.alive = 0;
+          o.death = DEATH_CUT;
+          if constexpr (TYPE == EP) annihilate<MODE>(o, t, pstep, seed);
+        }
+      }
+    }
+  }
+
+  // FP64 energy balance of the step, fixed order
+  double dep = (double)E;
+  dep = dep + o.mcr;
+  if (o.alive) dep = dep - (double)t.e;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < o.nsec) dep = dep - (double)o.sec(k).e;
+  dep = dep - o.esc;
+  dep = dep - o.cut;
+  dep = dep - o.mc;
+  o.dep = dep;
+
+  t.flags = (uint32_t)lim | ((uint32_t)proc << 4);
+  t.step = pstep + 1;
+}
+
+}  // namespace et

@@ -1,0 +1,24 @@
+// Kernel registry: each (mode, layout) translation unit fills one KernelSet
+// with its kernels' entry addresses; the host side launches through these.
+#pragma once
+
+namespace et {
+
+struct KernelSet {
+  const void* step[2][2][3];     // [instrumented][dense][type]
+  const void* persistent[2][2];  // [instrumented][dense]
+  const void* inject[2];         // [dense]
+};
+
+}  // namespace et
+
+extern "C" {
+void et_register_kernels_0_0(et::KernelSet*);
+void et_register_kernels_0_1(et::KernelSet*);
+void et_register_kernels_0_2(et::KernelSet*);
+void et_register_kernels_0_3(et::KernelSet*);
+void et_register_kernels_1_0(et::KernelSet*);
+void et_register_kernels_1_1(et::KernelSet*);
+void et_register_kernels_1_2(et::KernelSet*);
+void et_register_kernels_1_3(et::KernelSet*);
+}

@@ -1,0 +1,326 @@
+"""Python binding of the C ABI in include/et.h (argument marshalling only).
+
+Every transport step runs in the CUDA library libet.so built in-tree by
+paper_2302_08252_gb300/build.py; importing this module fails loudly when the
+library is missing.  PyTorch provides device memory (its caching allocator,
+through the et_config allocator callbacks) and the CUDA stream.
+
+Functions carry the C names; each raises EtError when the C call does not
+return ET_OK.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .workloads import PRIMARY_DTYPE
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libet.so")
+
+ET_OK, ET_ERR_INVALID, ET_ERR_CAPACITY, ET_ERR_CUDA, ET_ERR_TIMEOUT, ET_ERR_STATE, ET_ERR_NOMEM = \
+    range(7)
+FORM_SPARSE, FORM_DENSE = 0, 1
+LAYOUT_AOS, LAYOUT_SOA, LAYOUT_AOSOA32, LAYOUT_AOSOA64 = range(4)
+LAYOUTS = {"aos": 0, "soa": 1, "aosoa32": 2, "aosoa64": 3}
+MODE_STRICT, MODE_FAST = 0, 1
+DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT = range(3)
+DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2}
+N_LEAVES = 15
+LEAF_NAMES = ("x", "y", "z", "dx", "dy", "dz", "ekin", "num_ia_left", "id", "event", "step",
+              "slab", "time", "track_len", "flags")
+IDREC_DTYPE = np.dtype([("id", "<u8"), ("steps", "<u4"), ("type_death", "<u4")])
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class EtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"et status {status}: {msg}")
+        self.status = status
+
+
+class et_config(C.Structure):
+    _fields_ = [("capacity_log2", C.c_uint32), ("form", C.c_int32), ("layout", C.c_int32),
+                ("mode", C.c_int32), ("driver", C.c_int32), ("block_size", C.c_int32),
+                ("seed", C.c_uint64), ("max_events", C.c_uint32), ("max_iters", C.c_uint32),
+                ("instrument", C.c_int32), ("id_log", C.c_int32),
+                ("id_log_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class et_iter_stats(C.Structure):
+    _fields_ = [("n_active", C.c_uint32 * 3), ("pad", C.c_uint32), ("steps", C.c_uint64),
+                ("secondaries", C.c_uint64)]
+
+
+class et_ledger(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("injected", "deposited_cont", "below_cut", "escaped",
+                                          "mass_created", "mass_consumed")]
+
+
+class et_counters(C.Structure):
+    _fields_ = [("steps", C.c_uint64 * 3), ("secondaries", C.c_uint64 * 3),
+                ("iterations", C.c_uint64), ("slot_high_water", C.c_uint64 * 3),
+                ("reject_cap_hits", C.c_uint64), ("kernel_launches", C.c_uint64),
+                ("status", C.c_uint32), ("pad", C.c_uint32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2302_08252_gb300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    vp, st = C.c_void_p, C.c_int
+    sig = {
+        "et_create": ([C.POINTER(et_config), C.POINTER(vp)], st),
+        "et_destroy": ([vp], st),
+        "et_last_error": ([vp], C.c_char_p),
+        "et_create_geometry": ([vp, C.c_uint32, vp, vp, C.c_float], st),
+        "et_load_tables": ([vp, C.c_uint32, C.c_uint32, C.c_float, C.c_float, vp, vp], st),
+        "et_build_toy_tables": ([C.c_uint32, C.c_uint32, vp, vp, vp, vp], st),
+        "et_inject": ([vp, vp, C.c_size_t], st),
+        "et_inject_device": ([vp, vp, C.c_size_t], st),
+        "et_run_iteration": ([vp, C.POINTER(et_iter_stats)], st),
+        "et_run_until_empty": ([vp, C.c_uint64, C.POINTER(et_iter_stats), C.POINTER(C.c_uint64)], st),
+        "et_read_scoring": ([vp, C.c_uint32, vp, C.c_size_t, C.POINTER(et_ledger)], st),
+        "et_read_scoring_all": ([vp, vp, vp], st),
+        "et_read_iteration_counts": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
+        "et_read_id_log": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
+        "et_read_field_trace": ([vp, vp], st),
+        "et_read_heatmap": ([vp, C.c_uint32, C.c_uint32, vp, C.c_uint64], st),
+        "et_read_counters": ([vp, C.POINTER(et_counters)], st),
+        "et_reset": ([vp], st),
+        "et_set_timing": ([vp, C.c_int], st),
+        "et_read_timing": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)], st),
+        "et_debug_set_barrier_fault": ([vp, C.c_int, C.c_uint64], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Context:
+    """Owns an et_ctx* and keeps the allocator callbacks alive."""
+
+    def __init__(self, handle, callbacks):
+        self.handle = handle
+        self._callbacks = callbacks
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib.et_destroy(self.handle)
+            self.handle = None
+
+
+def _check(ctx, status):
+    if status != ET_OK:
+        h = ctx.handle if isinstance(ctx, Context) else ctx
+        msg = lib.et_last_error(h).decode() if h else ""
+        raise EtError(status, msg)
+
+
+def _torch_callbacks():
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return ALLOC_FN(alloc), FREE_FN(free)
+
+
+def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_STRICT,
+              driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
+              instrument=False, id_log=False, id_log_capacity=0, stream=None,
+              use_torch_allocator=True) -> Context:
+    """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
+    torch's current stream."""
+    import torch
+    if not torch.cuda.is_available():
+        raise EtError(ET_ERR_CUDA, "no CUDA device")
+    if stream is None:
+        s = torch.cuda.current_stream().cuda_stream
+    elif isinstance(stream, int):
+        s = stream
+    else:
+        s = stream.cuda_stream
+    cfg = et_config()
+    cfg.capacity_log2 = capacity_log2
+    cfg.form = form
+    cfg.layout = LAYOUTS[layout] if isinstance(layout, str) else layout
+    cfg.mode = mode
+    cfg.driver = DRIVERS[driver] if isinstance(driver, str) else driver
+    cfg.block_size = block_size
+    cfg.seed = seed
+    cfg.max_events = max_events
+    cfg.max_iters = max_iters
+    cfg.instrument = int(bool(instrument))
+    cfg.id_log = int(bool(id_log))
+    cfg.id_log_capacity = id_log_capacity
+    cfg.cuda_stream = s
+    cbs = None
+    if use_torch_allocator:
+        cbs = _torch_callbacks()
+        cfg.alloc, cfg.free = cbs
+    h = C.c_void_p()
+    st = lib.et_create(C.byref(cfg), C.byref(h))
+    ctx = Context(h, cbs)
+    _check(ctx, st)
+    return ctx
+
+
+def et_destroy(ctx: Context):
+    if ctx.handle:
+        st = lib.et_destroy(ctx.handle)
+        ctx.handle = None
+        if st != ET_OK:
+            raise EtError(st, "et_destroy")
+
+
+def et_create_geometry(ctx, thickness_mm, material, half_xy_mm):
+    th = np.ascontiguousarray(thickness_mm, dtype=np.float64)
+    mat = np.ascontiguousarray(material, dtype=np.uint8)
+    _check(ctx, lib.et_create_geometry(ctx.handle, len(th), _p(th), _p(mat), float(half_xy_mm)))
+
+
+def et_build_toy_tables(n_materials=2, n_nodes=257):
+    sig = np.zeros((n_materials, 5, n_nodes), dtype=np.float32)
+    dedx = np.zeros(n_materials, dtype=np.float32)
+    le = np.zeros(1, np.float32)
+    idl = np.zeros(1, np.float32)
+    st = lib.et_build_toy_tables(n_materials, n_nodes, _p(sig), _p(dedx), _p(le), _p(idl))
+    if st != ET_OK:
+        raise EtError(st, "et_build_toy_tables")
+    return {"sigma": sig, "dedx": dedx, "log_emin": float(le[0]), "inv_dlog": float(idl[0])}
+
+
+def et_load_tables(ctx, sigma, dedx, log_emin, inv_dlog):
+    sig = np.ascontiguousarray(sigma, dtype=np.float32)
+    d = np.ascontiguousarray(dedx, dtype=np.float32)
+    _check(ctx, lib.et_load_tables(ctx.handle, sig.shape[0], sig.shape[2], float(log_emin),
+                                   float(inv_dlog), _p(sig), _p(d)))
+
+
+def et_inject(ctx, primaries: np.ndarray):
+    p = np.ascontiguousarray(primaries)
+    assert p.dtype == PRIMARY_DTYPE
+    _check(ctx, lib.et_inject(ctx.handle, _p(p), len(p)))
+
+
+def et_inject_device(ctx, primaries_device, n: int):
+    """primaries_device: a CUDA torch.uint8 tensor holding n 48-byte records (or an int
+    device address)."""
+    ptr = primaries_device if isinstance(primaries_device, int) else primaries_device.data_ptr()
+    _check(ctx, lib.et_inject_device(ctx.handle, C.c_void_p(ptr), n))
+
+
+def et_run_iteration(ctx):
+    s = et_iter_stats()
+    _check(ctx, lib.et_run_iteration(ctx.handle, C.byref(s)))
+    return {"n_active": list(s.n_active), "steps": s.steps, "secondaries": s.secondaries}
+
+
+def et_run_until_empty(ctx, max_iters=1 << 30):
+    s = et_iter_stats()
+    n = C.c_uint64()
+    _check(ctx, lib.et_run_until_empty(ctx.handle, max_iters, C.byref(s), C.byref(n)))
+    return {"n_active": list(s.n_active), "steps": s.steps, "secondaries": s.secondaries,
+            "iterations": n.value}
+
+
+def et_read_scoring(ctx, event, n_slabs):
+    dep = np.zeros(n_slabs, dtype=np.float64)
+    lg = et_ledger()
+    _check(ctx, lib.et_read_scoring(ctx.handle, event, _p(dep), n_slabs, C.byref(lg)))
+    return dep, {f: getattr(lg, f) for f, _ in et_ledger._fields_}
+
+
+def et_read_scoring_all(ctx, max_events, n_slabs):
+    score = np.zeros((max_events, n_slabs), dtype=np.float64)
+    ledger = np.zeros((max_events, 6), dtype=np.float64)
+    _check(ctx, lib.et_read_scoring_all(ctx.handle, _p(score), _p(ledger)))
+    return score, ledger
+
+
+def et_read_iteration_counts(ctx):
+    n = C.c_uint64()
+    _check(ctx, lib.et_read_iteration_counts(ctx.handle, None, 0, C.byref(n)))
+    out = np.zeros((n.value, 3), dtype=np.uint64)
+    if n.value:
+        _check(ctx, lib.et_read_iteration_counts(ctx.handle, _p(out), n.value, C.byref(n)))
+    return out
+
+
+def et_read_id_log(ctx):
+    n = C.c_uint64()
+    _check(ctx, lib.et_read_id_log(ctx.handle, None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=IDREC_DTYPE)
+    if n.value:
+        _check(ctx, lib.et_read_id_log(ctx.handle, _p(out), n.value, C.byref(n)))
+    return out
+
+
+def et_read_field_trace(ctx):
+    out = np.zeros((3, N_LEAVES, 2), dtype=np.uint64)
+    _check(ctx, lib.et_read_field_trace(ctx.handle, _p(out)))
+    return out
+
+
+def et_read_heatmap(ctx, ptype, half, capacity):
+    out = np.zeros(capacity * 16, dtype=np.uint32)
+    _check(ctx, lib.et_read_heatmap(ctx.handle, ptype, half, _p(out), out.size))
+    return out
+
+
+def et_read_counters(ctx):
+    c = et_counters()
+    _check(ctx, lib.et_read_counters(ctx.handle, C.byref(c)))
+    return {"steps": list(c.steps), "secondaries": list(c.secondaries),
+            "iterations": c.iterations, "slot_high_water": list(c.slot_high_water),
+            "reject_cap_hits": c.reject_cap_hits, "kernel_launches": c.kernel_launches,
+            "status": c.status}
+
+
+def et_reset(ctx):
+    _check(ctx, lib.et_reset(ctx.handle))
+
+
+def et_set_timing(ctx, on=True):
+    _check(ctx, lib.et_set_timing(ctx.handle, int(bool(on))))
+
+
+def et_read_timing(ctx):
+    ms = C.c_double()
+    n = C.c_uint64()
+    _check(ctx, lib.et_read_timing(ctx.handle, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def et_debug_set_barrier_fault(ctx, skip_block=-1, timeout_ns=0):
+    _check(ctx, lib.et_debug_set_barrier_fault(ctx.handle, skip_block, timeout_ns))
+
+
+def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) -> Context:
+    """Create a context and load the calorimeter and the toy tables (convenience)."""
+    ctx = et_create(max_events=max_events, **kw)
+    et_create_geometry(ctx, geom["thickness"], geom["material"], geom["half_xy"])
+    t = tables if tables is not None else et_build_toy_tables()
+    et_load_tables(ctx, t["sigma"], t["dedx"], t["log_emin"], t["inv_dlog"])
+    return ctx
