@@ -115,6 +115,7 @@ struct Args {
   unsigned long long* trace;    // [3][15][2] or NULL
   uint32_t* heat[NTYPES][2];    // per-word access counts or NULL
   unsigned long long timeout_ns;// bounded waits (persistent driver)
+  unsigned long long* iter_ns;  // persistent driver: %globaltimer at each iteration start, or NULL
 };
 
 constexpr int MAX_SLABS = 128;

@@ -61,6 +61,7 @@ struct et_ctx {
   uint64_t timed = 0;
   uint64_t launches = 0;
   int fault_skip_block = -1;  // fault injection for the persistent driver's barrier (tests)
+  unsigned long long* d_iter_ns = nullptr;
 };
 
 static et_status fail(et_ctx* c, et_status s, const char* fmt, ...) {
@@ -263,10 +264,8 @@ et_status et_reset(et_ctx* c) {
       if (a.heat[t][h])
         CUDA_TRY(c, cudaMemsetAsync(a.heat[t][h], 0, (size_t)c->cap * 64u, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  timing_collect(c);  // kernel timing accumulates across resets until et_read_timing
   c->launches = 0;
-  c->ev_used = 0;
-  c->ms_acc = 0.0;
-  c->timed = 0;
   memset(c->h_ctl, 0, sizeof(DevCtl));
   return ET_OK;
 }
@@ -352,17 +351,20 @@ et_status et_load_tables(et_ctx* c, uint32_t n_materials, uint32_t n_nodes, floa
   a.n_mat = n_materials;
   a.log_emin = log_emin;
   a.inv_dlog = inv_dlog;
-  c->smem_all = smem_bytes((int)n_materials);
+  // dynamic shared memory: tables, then one interaction queue per warp
+  c->smem_all = tables_bytes_aligned((int)n_materials) + (size_t)(c->block / 32) * queue_bytes_per_warp();
   c->smem_g = c->smem_all;
   c->smem_e = c->smem_all;
+  const void* pf = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+  CUDA_TRY(c, cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_all));
   // grids: grid-stride kernels sized to fill the machine
   int occ = 0;
   for (int t = 0; t < 3; ++t) {
     const void* fn = c->ks.step[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0][t];
+    CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_all));
     CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->block, c->smem_all));
     c->grid_fixed[t] = (occ > 0 ? occ : 1) * c->num_sms;
   }
-  const void* pf = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
   CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pf, c->block, c->smem_all));
   if (occ < 1) return fail(c, ET_ERR_CUDA, "persistent kernel does not fit on an SM");
   c->grid_persistent = occ * c->num_sms;
@@ -718,6 +720,30 @@ et_status et_read_timing(et_ctx* c, double* ms_total, uint64_t* launches) {
   if (launches) *launches = c->timed;
   c->ms_acc = 0.0;
   c->timed = 0;
+  return ET_OK;
+}
+
+// Profiling hooks (not in et.h): per-iteration start times of the persistent driver.
+et_status et_debug_iteration_times(et_ctx* c, int enable) {
+  if (!c) return ET_ERR_INVALID;
+  if (enable && !c->d_iter_ns) {
+    c->d_iter_ns = (unsigned long long*)dalloc(c, (size_t)c->cfg.max_iters * 8u);
+    if (!c->d_iter_ns) return fail(c, ET_ERR_NOMEM, "iteration time log");
+  }
+  c->args.iter_ns = enable ? c->d_iter_ns : nullptr;
+  return ET_OK;
+}
+
+et_status et_debug_read_iteration_times(et_ctx* c, uint64_t* out, uint64_t cap, uint64_t* n) {
+  if (!c || !n) return ET_ERR_INVALID;
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  uint64_t it = c->h_ctl->iter;
+  if (it > c->cfg.max_iters) it = c->cfg.max_iters;
+  *n = it;
+  if (!out || !c->d_iter_ns) return ET_OK;
+  if (cap < it) return fail(c, ET_ERR_CAPACITY, "buffer too short");
+  CUDA_TRY(c, cudaMemcpy(out, c->d_iter_ns, it * 8u, cudaMemcpyDeviceToHost));
   return ET_OK;
 }
 

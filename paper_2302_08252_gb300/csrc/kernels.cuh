@@ -97,13 +97,14 @@ __device__ __forceinline__ uint32_t& pick(int ty, uint32_t& a0, uint32_t& a1, ui
   return ty == 0 ? a0 : (ty == 1 ? a1 : a2);
 }
 
-__device__ __forceinline__ Trk make_secondary(const Trk& parent, const Sec& s) {
+// Secondary k of a parent that has just taken its step (parent.step already advanced).
+__device__ __forceinline__ Trk make_secondary(const Trk& parent, const Sec& s, int k) {
   Trk r;
   r.x = parent.x; r.y = parent.y; r.z = parent.z;
   r.dx = s.dx; r.dy = s.dy; r.dz = s.dz;
   r.e = s.e;
   r.nia = -1.0f;
-  r.id = s.id;
+  r.id = secondary_id(parent.id, parent.step - 1u, (uint32_t)k);
   r.event = parent.event;
   r.step = 0;
   r.slab = parent.slab;
@@ -115,14 +116,16 @@ __device__ __forceinline__ Trk make_secondary(const Trk& parent, const Sec& s) {
 
 __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const StepOut& o) {
   const size_t ev = t.event;
-  if (o.dep != 0.0) atomicAdd(&a.score[ev * a.n_slabs + (size_t)o.slab_cont], o.dep);
-  if (o.cut != 0.0) {
-    atomicAdd(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
-    atomicAdd(&a.ledger[ev * 5 + 1], o.cut);
+  if (o.dep_nz) atomicAdd(&a.score[ev * a.n_slabs + (size_t)o.slab_cont], o.dep);
+  if (o.bal) {
+    if ((o.bal & B_CUT) && o.cut != 0.0) {
+      atomicAdd(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
+      atomicAdd(&a.ledger[ev * 5 + 1], o.cut);
+    }
+    if ((o.bal & B_ESC) && o.esc != 0.0f) atomicAdd(&a.ledger[ev * 5 + 2], (double)o.esc);
+    if (o.bal & B_MCR) atomicAdd(&a.ledger[ev * 5 + 3], (double)MC2 + (double)MC2);
+    if ((o.bal & B_MC) && o.mc != 0.0) atomicAdd(&a.ledger[ev * 5 + 4], o.mc);
   }
-  if (o.esc != 0.0) atomicAdd(&a.ledger[ev * 5 + 2], o.esc);
-  if (o.mcr != 0.0) atomicAdd(&a.ledger[ev * 5 + 3], o.mcr);
-  if (o.mc != 0.0) atomicAdd(&a.ledger[ev * 5 + 4], o.mc);
 }
 
 // warp-aggregated append of death records
@@ -162,69 +165,149 @@ __device__ __forceinline__ void count_secondaries(const Args& a, uint32_t packed
   if (rj && lane == 0) atomicAdd(&a.ctl->reject_cap_hits, (unsigned long long)__popc(rj));
 }
 
+// Pointer tables of the kernel arguments indexed by a run-time (warp-uniform) type:
+// selects between constant-offset parameter reads, no indexed parameter access.
+template <typename T>
+__device__ __forceinline__ T sel3(int ty, T v0, T v1, T v2) {
+  return ty == 0 ? v0 : (ty == 1 ? v1 : v2);
+}
+__device__ __forceinline__ char* trk_of(const Args& a, int type, int half) {
+  return half ? sel3(type, a.trk[0][1], a.trk[1][1], a.trk[2][1])
+              : sel3(type, a.trk[0][0], a.trk[1][0], a.trk[2][0]);
+}
+__device__ __forceinline__ uint32_t* idx_of(const Args& a, int type, int half) {
+  return half ? sel3(type, a.idx[0][1], a.idx[1][1], a.idx[2][1])
+              : sel3(type, a.idx[0][0], a.idx[1][0], a.idx[2][0]);
+}
+
 template <int L, bool INSTR>
 __device__ __forceinline__ View<L, INSTR> view_of(const Args& a, int type, int half) {
   View<L, INSTR> v;
-  v.base = half ? a.trk[type][1] : a.trk[type][0];
+  v.base = trk_of(a, type, half);
   v.cap = a.cap;
   v.ins.trace = a.trace;
-  v.ins.heat = INSTR ? (half ? a.heat[type][1] : a.heat[type][0]) : nullptr;
+  v.ins.heat = nullptr;
+  if (INSTR)
+    v.ins.heat = half ? sel3(type, a.heat[0][1], a.heat[1][1], a.heat[2][1])
+                      : sel3(type, a.heat[0][0], a.heat[1][0], a.heat[2][0]);
   v.ins.type = type;
   return v;
 }
 
-// One warp steps up to 32 tracks of type TYPE (lanes with valid == false idle).
-template <int TYPE, int MODE, int L, bool INSTR, bool DENSE>
-__device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, uint32_t it, uint32_t i,
-                                             bool valid, uint32_t lane) {
-  const uint32_t hc = it & 1u, hn = hc ^ 1u;
+// ---- per-warp interaction queue ----
+// Lanes whose step ends in a discrete interaction park (post-transport track,
+// interaction context, slot) in a shared-memory ring of QCAP entries per warp,
+// stored field-major so that 32 lanes touch 32 consecutive words.  Whenever 32
+// entries wait, the warp drains them with every lane busy; a partial queue is
+// drained when the warp moves to another particle type or runs out of chunks.
+// This keeps the long interaction code (Compton rejection, rotations, pair,
+// brems) from running with most lanes of a warp idle.
+constexpr uint32_t QCAP = 64;
+constexpr uint32_t QW = 24;  // 16 track words, 7 context words, slot
+
+__host__ __device__ constexpr size_t queue_bytes_per_warp() { return (size_t)QW * QCAP * 4u; }
+__host__ __device__ inline size_t tables_bytes_aligned(int n_mat) {
+  return (smem_bytes(n_mat) + 15u) & ~(size_t)15u;
+}
+
+struct WarpQueue {
+  uint32_t* q;  // [QW][QCAP]
+  uint32_t head, count;  // warp-uniform
+};
+
+__device__ __forceinline__ void q_put(uint32_t* q, uint32_t s, const Trk& t, const Ctx& cx,
+                                      uint32_t slot) {
+  q[0 * QCAP + s] = __float_as_uint(t.x);
+  q[1 * QCAP + s] = __float_as_uint(t.y);
+  q[2 * QCAP + s] = __float_as_uint(t.z);
+  q[3 * QCAP + s] = __float_as_uint(t.dx);
+  q[4 * QCAP + s] = __float_as_uint(t.dy);
+  q[5 * QCAP + s] = __float_as_uint(t.dz);
+  q[6 * QCAP + s] = __float_as_uint(t.e);
+  q[7 * QCAP + s] = __float_as_uint(t.nia);
+  q[8 * QCAP + s] = (uint32_t)t.id;
+  q[9 * QCAP + s] = (uint32_t)(t.id >> 32);
+  q[10 * QCAP + s] = t.event;
+  q[11 * QCAP + s] = t.step;
+  q[12 * QCAP + s] = (uint32_t)t.slab;
+  q[13 * QCAP + s] = __float_as_uint(t.time);
+  q[14 * QCAP + s] = __float_as_uint(t.len);
+  q[15 * QCAP + s] = t.flags;
+  q[16 * QCAP + s] = __float_as_uint(cx.E);
+  q[17 * QCAP + s] = __float_as_uint(cx.sig);
+  q[18 * QCAP + s] = __float_as_uint(cx.sc);
+  q[19 * QCAP + s] = __float_as_uint(cx.sp);
+  q[20 * QCAP + s] = __float_as_uint(cx.u1);
+  q[21 * QCAP + s] = __float_as_uint(cx.u2);
+  q[22 * QCAP + s] = __float_as_uint(cx.u3);
+  q[23 * QCAP + s] = slot;
+}
+
+__device__ __forceinline__ void q_get(const uint32_t* q, uint32_t s, Trk& t, Ctx& cx,
+                                      uint32_t& slot) {
+  t.x = __uint_as_float(q[0 * QCAP + s]);
+  t.y = __uint_as_float(q[1 * QCAP + s]);
+  t.z = __uint_as_float(q[2 * QCAP + s]);
+  t.dx = __uint_as_float(q[3 * QCAP + s]);
+  t.dy = __uint_as_float(q[4 * QCAP + s]);
+  t.dz = __uint_as_float(q[5 * QCAP + s]);
+  t.e = __uint_as_float(q[6 * QCAP + s]);
+  t.nia = __uint_as_float(q[7 * QCAP + s]);
+  t.id = (uint64_t)q[8 * QCAP + s] | ((uint64_t)q[9 * QCAP + s] << 32);
+  t.event = q[10 * QCAP + s];
+  t.step = q[11 * QCAP + s];
+  t.slab = (int32_t)q[12 * QCAP + s];
+  t.time = __uint_as_float(q[13 * QCAP + s]);
+  t.len = __uint_as_float(q[14 * QCAP + s]);
+  t.flags = q[15 * QCAP + s];
+  cx.E = __uint_as_float(q[16 * QCAP + s]);
+  cx.sig = __uint_as_float(q[17 * QCAP + s]);
+  cx.sc = __uint_as_float(q[18 * QCAP + s]);
+  cx.sp = __uint_as_float(q[19 * QCAP + s]);
+  cx.u1 = __uint_as_float(q[20 * QCAP + s]);
+  cx.u2 = __uint_as_float(q[21 * QCAP + s]);
+  cx.u3 = __uint_as_float(q[22 * QCAP + s]);
+  slot = q[23 * QCAP + s];
+}
+
+// Everything after the physics of a finished step, for the lanes with act == true:
+// deposits, death records, counters, slot allocation and the writes of the survivor
+// and the secondaries.  All 32 lanes of the warp call it together; `type` is
+// warp-uniform.
+template <int L, bool INSTR, bool DENSE>
+__device__ __forceinline__ void finish(const Args& a, const int type, uint32_t it, uint32_t lane,
+                                       bool act, const Trk& t, const StepOut& o, uint32_t slot) {
+  const uint32_t hn = (it & 1u) ^ 1u;
   const uint32_t nslot = (it + 1) % 3;
   DevCtl* ctl = a.ctl;
-  Trk t;
-  StepOut o;
-  uint32_t slot = 0;
-  if (valid) {
-    if constexpr (DENSE) {
-      slot = i;
-      t = view_of<L, INSTR>(a, TYPE, (int)hc).load(slot);
-    } else {
-      slot = __ldcg((hc ? a.idx[TYPE][1] : a.idx[TYPE][0]) + i);
-      t = view_of<L, INSTR>(a, TYPE, 0).load(slot);
-    }
-    step_track<TYPE, MODE>(t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o);
-    score_step(a, t, o);
-  } else {
-    o.alive = 0;
-    o.nsec = 0;
-    o.reject = 0;
-    o.death = ALIVE;
-  }
-  if (a.idlog) log_deaths(a, valid && !o.alive, t, TYPE, o.death, lane);
+  if (act) score_step(a, t, o);
+  const bool alive = act && o.alive;
+  const int nsec = act ? o.nsec : 0;
+  if (a.idlog) log_deaths(a, act && !o.alive, t, type, act ? o.death : 0, lane);
 
   // per-type record counts of this lane: survivor + secondaries
-  uint32_t packed = (valid && o.alive) ? (1u << (10 * TYPE)) : 0u;
   uint32_t packed_sec = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    if (k < o.nsec) packed_sec += 1u << (10 * o.sec(k).type);
-  packed += packed_sec;
-  count_secondaries(a, packed_sec, valid ? o.reject : 0, lane);
+    if (k < nsec) packed_sec += 1u << (10 * o.type(k));
+  const uint32_t packed = (alive ? (1u << (10 * type)) : 0u) + packed_sec;
+  count_secondaries(a, packed_sec, act ? o.reject : 0, lane);
 
   uint32_t q0, q1, q2;  // positions in the next arrays (dense) / next slot lists (sparse)
   warp_reserve(packed, lane, ctl->cnt[nslot], q0, q1, q2);
 
   if constexpr (DENSE) {
-    if (valid && o.alive) {
-      const uint32_t at = pick(TYPE, q0, q1, q2)++;
-      if (at < a.cap) view_of<L, INSTR>(a, TYPE, (int)hn).store(at, t);
+    if (alive) {
+      const uint32_t at = pick(type, q0, q1, q2)++;
+      if (at < a.cap) view_of<L, INSTR>(a, type, (int)hn).store(at, t);
       else atomicOr(&ctl->status, ST_CAPACITY);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      if (k < o.nsec) {
-        const int ty = o.sec(k).type;
+      if (k < nsec) {
+        const int ty = o.type(k);
         const uint32_t at = pick(ty, q0, q1, q2)++;
-        if (at < a.cap) view_of<L, INSTR>(a, ty, (int)hn).store(at, make_secondary(t, o.sec(k)));
+        if (at < a.cap) view_of<L, INSTR>(a, ty, (int)hn).store(at, make_secondary(t, o.sec(k), k));
         else atomicOr(&ctl->status, ST_CAPACITY);
       }
     }
@@ -232,27 +315,85 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, uint
     // fresh slots for the secondaries
     uint32_t s0, s1, s2;
     warp_reserve(packed_sec, lane, ctl->hwm, s0, s1, s2);
-    if (valid && o.alive) {
-      view_of<L, INSTR>(a, TYPE, 0).store_leaves(slot, t, o.dirty);
-      const uint32_t at = pick(TYPE, q0, q1, q2)++;
-      if (at < a.cap) (hn ? a.idx[TYPE][1] : a.idx[TYPE][0])[at] = slot;
+    if (alive) {
+      view_of<L, INSTR>(a, type, 0).store_leaves(slot, t, o.dirty);
+      const uint32_t at = pick(type, q0, q1, q2)++;
+      if (at < a.cap) idx_of(a, type, (int)hn)[at] = slot;
       else atomicOr(&ctl->status, ST_CAPACITY);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      if (k < o.nsec) {
-        const int ty = o.sec(k).type;
+      if (k < nsec) {
+        const int ty = o.type(k);
         const uint32_t ns = pick(ty, s0, s1, s2)++;
         const uint32_t at = pick(ty, q0, q1, q2)++;
         if (ns < a.cap && at < a.cap) {
-          view_of<L, INSTR>(a, ty, 0).store(ns, make_secondary(t, o.sec(k)));
-          (hn ? a.idx[ty][1] : a.idx[ty][0])[at] = ns;
+          view_of<L, INSTR>(a, ty, 0).store(ns, make_secondary(t, o.sec(k), k));
+          idx_of(a, ty, (int)hn)[at] = ns;
         } else {
           atomicOr(&ctl->status, ST_CAPACITY);
         }
       }
     }
   }
+}
+
+// One warp transports up to 32 tracks of one type (lanes with valid == false idle).
+// Lanes whose step ends in a discrete interaction go into the warp's queue; the
+// queue is drained 32 entries at a time, or completely when `drain_all` is set (end
+// of the warp's work in a type, or sparse iterations where batching cannot fill a
+// warp).  With no valid lane this call only drains.
+template <int MODE, int L, bool INSTR, bool DENSE>
+__device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, const int type,
+                                             uint32_t it, uint32_t i, bool valid, uint32_t lane,
+                                             WarpQueue& wq, bool drain_all) {
+  const uint32_t hc = it & 1u;
+  Trk t;
+  StepOut o;
+  Ctx cx;
+  uint32_t slot = 0;
+  bool inter = false;
+  if (valid) {
+    if constexpr (DENSE) {
+      slot = i;
+      t = view_of<L, INSTR>(a, type, (int)hc).load(slot);
+    } else {
+      slot = __ldcg(idx_of(a, type, (int)hc) + i);
+      t = view_of<L, INSTR>(a, type, 0).load(slot);
+    }
+    inter = transport<MODE>(type, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
+  }
+  finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot);
+  const uint32_t mask = __ballot_sync(FULL, inter);
+  if (inter) {
+    const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
+    q_put(wq.q, pos, t, cx, slot);
+  }
+  wq.count += (uint32_t)__popc(mask);
+  __syncwarp();
+  while (wq.count >= 32u || (drain_all && wq.count)) {
+    // interactions of the n oldest entries, one per lane
+    const uint32_t n = wq.count >= 32u ? 32u : wq.count;
+    const bool act = lane < n;
+    uint32_t qslot = 0;
+    if (act) {
+      q_get(wq.q, (wq.head + lane) % QCAP, t, cx, qslot);
+      interact<MODE>(type, t, cx, a.seed_lo, o);
+    }
+    __syncwarp();  // entries consumed before their ring slots are reused
+    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, qslot);
+    wq.head = (wq.head + n) % QCAP;
+    wq.count -= n;
+  }
+}
+
+__device__ __forceinline__ WarpQueue warp_queue(unsigned char* smem, int n_mat) {
+  WarpQueue wq;
+  wq.q = reinterpret_cast<uint32_t*>(smem + tables_bytes_aligned(n_mat) +
+                                     (threadIdx.x >> 5) * queue_bytes_per_warp());
+  wq.head = 0;
+  wq.count = 0;
+  return wq;
 }
 
 // ---- per-type step kernel (host-loop and graph drivers) ----
@@ -268,9 +409,17 @@ __global__ void __launch_bounds__(256) k_step(const __grid_constant__ Args a) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t c = gw; c * 32u < n; c += nw) {
+  WarpQueue wq = warp_queue(smem, (int)a.n_mat);
+  const uint32_t chunks = (n + 31u) / 32u;
+  const bool batch = chunks >= 2u * nw;  // each warp sees several chunks: batching pays
+  uint32_t c = gw;
+  while (c < chunks || wq.count) {
+    const bool more = c < chunks;
     const uint32_t i = c * 32u + lane;
-    process_warp<TYPE, MODE, L, INSTR, DENSE>(a, tb, it, i, i < n, lane);
+    const bool last = !more || c + nw >= chunks;
+    process_warp<MODE, L, INSTR, DENSE>(a, tb, TYPE, it, i, more && i < n, lane, wq,
+                                        last || !batch);
+    c += nw;
   }
 }
 
@@ -341,14 +490,19 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
 
 // ---- persistent kernel: all types, all iterations, one cooperative launch ----
 // Warp chunks of 32 tracks are type-uniform: the iteration's index space is
-// [ceil(n_e-/32) chunks of e-][chunks of e+][chunks of gamma].
+// [ceil(n_e-/32) chunks of e-][chunks of e+][chunks of gamma].  Warps take chunks
+// dynamically from a per-iteration counter (one atomic per chunk, issued one chunk
+// ahead so that its latency hides behind the current chunk), which evens out the
+// uneven cost of chunks before the grid barrier.
 template <int MODE, int L, bool INSTR, bool DENSE>
-__global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Args a,
+// Two resident blocks of 256 threads per SM (<= 128 registers per thread).
+__global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ Args a,
                                                     int fault_skip_block) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_n[3];
   __shared__ uint32_t s_stop;
   const Tabs tb = stage_tables<true, true>(smem, a);
+  WarpQueue wq = warp_queue(smem, (int)a.n_mat);
   DevCtl* c = a.ctl;
   uint32_t* snap = &c->status_snap;
   const uint32_t lane = threadIdx.x & 31u;
@@ -371,6 +525,7 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Args
     if (s_stop) break;
     const uint32_t n0 = min(s_n[0], a.cap), n1 = min(s_n[1], a.cap), n2 = min(s_n[2], a.cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (a.iter_ns && it < a.max_iters) a.iter_ns[it] = global_ns();
       for (int t = 0; t < 3; ++t) {
         c->cnt[(it + 2) % 3][t] = 0;
         c->steps[t] += s_n[t];
@@ -380,17 +535,31 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Args
     }
     const uint32_t w0 = (n0 + 31) / 32, w1 = (n1 + 31) / 32, w2 = (n2 + 31) / 32;
     const uint32_t wt = w0 + w1 + w2;
-    for (uint32_t ch = gw; ch < wt; ch += nw) {
-      if (ch < w0) {
-        const uint32_t i = ch * 32u + lane;
-        process_warp<EM, MODE, L, INSTR, DENSE>(a, tb, it, i, i < n0, lane);
-      } else if (ch < w0 + w1) {
-        const uint32_t i = (ch - w0) * 32u + lane;
-        process_warp<EP, MODE, L, INSTR, DENSE>(a, tb, it, i, i < n1, lane);
-      } else {
-        const uint32_t i = (ch - w0 - w1) * 32u + lane;
-        process_warp<GAM, MODE, L, INSTR, DENSE>(a, tb, it, i, i < n2, lane);
+    // static chunk order: warp w takes chunks w, w + nw, ...; the type changes at most
+    // twice per warp and iteration, and the queue is emptied at each change
+    const bool batch = wt >= 2u * nw;  // each warp sees several chunks: batching pays
+    uint32_t ch = gw;
+    int qtype = EM;
+    while (ch < wt || wq.count) {
+      int ty = qtype;
+      uint32_t i = 0;
+      bool valid = false, drain_all = true;
+      if (ch < wt) {
+        const int cty = ch < w0 ? EM : (ch < w0 + w1 ? EP : GAM);
+        if (cty == qtype || wq.count == 0) {
+          ty = qtype = cty;
+          const uint32_t base = ty == EM ? 0u : (ty == EP ? w0 : w0 + w1);
+          const uint32_t nt = ty == EM ? n0 : (ty == EP ? n1 : n2);
+          i = (ch - base) * 32u + lane;
+          valid = i < nt;
+          const uint32_t nxt = ch + nw;
+          const int nty = nxt < wt ? (nxt < w0 ? EM : (nxt < w0 + w1 ? EP : GAM)) : -1;
+          drain_all = !batch || nty != ty;  // the warp's last chunk of this type
+          ch = nxt;
+        }
+        // else: drain the previous type's queue first; this chunk is taken next round
       }
+      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, drain_all);
     }
     if (!grid_sync(c, gridDim.x, a.timeout_ns, snap)) return;
     if (DENSE && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -405,7 +574,7 @@ __global__ void __launch_bounds__(256) k_persistent(const __grid_constant__ Args
     c->iter = it;
     const uint32_t cur = it % 3;
     for (int t = 0; t < 3; ++t) c->cnt[(it + 2) % 3][t] = 0;  // between iterations only cur is non-zero
-    c->done = (__ldcg(&c->cnt[cur][0]) + __ldcg(&c->cnt[cur][1]) + __ldcg(&c->cnt[cur][2]) == 0);
+    c->done =(__ldcg(&c->cnt[cur][0]) + __ldcg(&c->cnt[cur][1]) + __ldcg(&c->cnt[cur][2]) == 0);
   }
 }
 

@@ -5,13 +5,18 @@
 // division and square root), so results are bit-identical to the model's
 // definition; fast mode swaps in hardware intrinsics and allows FMA.
 //
-// Per step: Philox block 0 of (seed, event | id, step) -> interaction lengths,
-// cross section from the shared-memory tables, distances to the slab planes and
-// box faces, the step limiter in fixed order, move, continuous loss, boundary
-// crossing, then at most one discrete interaction (photon: Compton by
-// Butcher-Messel rejection, pair, photoelectric; e+-: bremsstrahlung with a 1/k
-// spectrum; positrons annihilate at rest below the cut).  The FP64 energy
-// balance of the step is the deposit.
+// The step is split in two so that the kernels can compact the lanes that
+// need a discrete interaction (see kernels.cuh):
+//   transport(): Philox block 0 of (seed, event | id, step), interaction
+//     lengths, cross section from the shared-memory tables, distances to the
+//     slab planes and box faces, the step limiter in fixed order, move,
+//     continuous loss, boundary crossing, deaths (escape; e+- below the cut,
+//     positrons annihilating at rest).  It finishes the step unless a discrete
+//     interaction is due, in which case it returns the interaction context.
+//   interact(): photon Compton (Butcher-Messel rejection), pair or
+//     photoelectric; e+- bremsstrahlung with a 1/k spectrum; the step's FP64
+//     energy balance.
+// Composed, the two are exactly the model's single step.
 #pragma once
 
 #include "common.cuh"
@@ -36,22 +41,50 @@ struct Tabs {
   int n_slabs;
 };
 
+// A secondary's id is derived when it is written: secondary_id(parent, step, ordinal).
 struct Sec {
   float e, dx, dy, dz;
-  uint64_t id;
-  int type;
 };
+
+// Terms of the step's energy balance other than the survivor and the secondaries.
+enum : uint32_t { B_CUT = 1u, B_ESC = 2u, B_MC = 4u, B_MCR = 8u };
 
 // At most 3 secondaries per step (brems photon + 2 annihilation photons; e- + 2
 // annihilation photons from a pair whose positron is below the cut).  They sit in
-// three named slots, never an indexed array, so that they stay in registers.
+// three named slots, never an indexed array, so that they stay in registers; their
+// types are packed 2 bits each.
 struct StepOut {
   int alive, death, nsec, reject, slab_cont;
-  uint32_t dirty;
+  uint32_t dirty, types, bal;
+  bool dep_nz;      // dep != 0
   Sec s0, s1, s2;
-  double dep, cut, esc, mc, mcr;
+  double dep;       // FP64 balance: deposited in the pre-step slab
+  double cut;       // below-cut energy, deposited in the end slab (B_CUT)
+  double mc;        // rest mass consumed by pair production (B_MC)
+  float esc;        // escaped energy (B_ESC)
   // k must be a compile-time constant after unrolling
   __device__ __forceinline__ const Sec& sec(int k) const { return k == 0 ? s0 : (k == 1 ? s1 : s2); }
+  __device__ __forceinline__ int type(int k) const { return (int)((types >> (2 * k)) & 3u); }
+  __device__ __forceinline__ void add_cut(float x) {
+    cut = (bal & B_CUT) ? cut + (double)x : (double)x;  // 0 + x == x: same as summing from 0
+    bal |= B_CUT;
+  }
+  __device__ __forceinline__ void begin() {
+    alive = 1;
+    death = ALIVE;
+    nsec = 0;
+    reject = 0;
+    types = 0;
+    bal = 0;
+    dep_nz = false;
+  }
+};
+
+// What transport() hands to interact() when a discrete interaction is due.
+struct Ctx {
+  float E;              // pre-step energy
+  float sig, sc, sp;    // photon: total, Compton, pair cross sections at E; e+-: brems
+  float u1, u2, u3;     // Philox block 0, words 1..3
 };
 
 template <int MODE>
@@ -70,19 +103,18 @@ __device__ __forceinline__ void m_sincos2pi(float u, float* s, float* c) {
   else __sincosf(6.28318530717958648f * u, s, c);
 }
 
-__device__ __forceinline__ void add_sec(StepOut& o, const Trk& t, uint32_t pstep, int type,
-                                        float e, float dx, float dy, float dz) {
+__device__ __forceinline__ void add_sec(StepOut& o, int type, float e, float dx, float dy,
+                                        float dz) {
   const int k = o.nsec;
   Sec s;
   s.e = e;
   s.dx = dx;
   s.dy = dy;
   s.dz = dz;
-  s.id = secondary_id(t.id, pstep, (uint32_t)k);
-  s.type = type;
   if (k == 0) o.s0 = s;
   else if (k == 1) o.s1 = s;
   else o.s2 = s;
+  o.types |= (uint32_t)type << (2 * k);
   o.nsec = k + 1;
 }
 
@@ -102,6 +134,7 @@ __device__ __forceinline__ void rotate_about(float ux, float uy, float uz, float
   }
 }
 
+// Positron at rest: two back-to-back photons of m_e c^2, isotropic (Philox block 65).
 template <int MODE>
 __device__ __forceinline__ void annihilate(StepOut& o, const Trk& t, uint32_t pstep,
                                            uint32_t seed) {
@@ -111,24 +144,49 @@ __device__ __forceinline__ void annihilate(StepOut& o, const Trk& t, uint32_t ps
   float sp, cp;
   m_sincos2pi<MODE>(u01(r.y), &sp, &cp);
   const float dx = sint * cp, dy = sint * sp, dz = cost;
-  add_sec(o, t, pstep, GAM, MC2, dx, dy, dz);
-  add_sec(o, t, pstep, GAM, MC2, -dx, -dy, -dz);
-  o.mcr = (double)MC2 + (double)MC2;
+  add_sec(o, GAM, MC2, dx, dy, dz);
+  add_sec(o, GAM, MC2, -dx, -dy, -dz);
+  o.bal |= B_MCR;
 }
 
-template <int TYPE, int MODE>
-__device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emin, float inv_dlog,
-                                           float half, uint32_t seed, StepOut& o) {
-  constexpr bool charged = TYPE != GAM;
-  o.alive = 1;
-  o.death = ALIVE;
-  o.nsec = 0;
-  o.reject = 0;
-  o.dep = o.cut = o.esc = o.mc = o.mcr = 0.0;
+// FP64 energy balance of the step, fixed order:
+//   dep = E + mcr - E_survivor - sum E_secondaries - esc - cut - mc
+__device__ __forceinline__ void balance(const Trk& t, float E, StepOut& o) {
+  if (o.bal == 0 && o.nsec == 0 && o.alive) {
+    // only continuous loss: the balance is E - E'.  Subtracting the zero terms leaves it
+    // unchanged, and E - E' is exact in FP32 when E' >= E/2 (Sterbenz), so no FP64
+    // arithmetic is needed on this, the common, path.
+    const float e1 = t.e;
+    o.dep_nz = e1 != E;
+    if (e1 >= 0.5f * E) o.dep = (double)(E - e1);
+    else o.dep = (double)E - (double)e1;
+  } else {
+    double dep = (double)E;
+    if (o.bal & B_MCR) dep = dep + ((double)MC2 + (double)MC2);
+    if (o.alive) dep = dep - (double)t.e;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < o.nsec) dep = dep - (double)o.sec(k).e;
+    if (o.bal & B_ESC) dep = dep - (double)o.esc;
+    if (o.bal & B_CUT) dep = dep - o.cut;
+    if (o.bal & B_MC) dep = dep - o.mc;
+    o.dep = dep;
+    o.dep_nz = dep != 0.0;
+  }
+}
+
+// Returns true when a discrete interaction is due: the step is then unfinished
+// (step counter and flags unchanged) and cx holds what interact() needs.
+// `type` is warp-uniform; a compile-time constant at the per-type kernels' call sites.
+template <int MODE>
+__device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb, float log_emin,
+                                          float inv_dlog, float half, uint32_t seed, StepOut& o,
+                                          Ctx& cx) {
+  const bool charged = type != GAM;
+  o.begin();
   o.dirty = D_POS | D_NIA | D_STEP | D_TIME | D_LEN | D_FLAGS;
   const uint32_t pstep = t.step;
-  const uint32_t idlo = (uint32_t)t.id, idhi = (uint32_t)(t.id >> 32);
-  const uint4 r0 = philox(idlo, idhi, pstep, 0u, seed, t.event);
+  const uint4 r0 = philox((uint32_t)t.id, (uint32_t)(t.id >> 32), pstep, 0u, seed, t.event);
   const float E = t.e;
 
   // interaction lengths left
@@ -143,7 +201,7 @@ __device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emi
   bin = bin > NBINS - 1 ? NBINS - 1 : bin;
   const float f = lx - (float)bin;
   float sig;
-  if constexpr (charged) {
+  if (charged) {
     const float2 b = tb.brem[m * NBINS + bin];
     sig = b.x + f * b.y;
   } else {
@@ -173,7 +231,7 @@ __device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emi
   if (sx < s) { s = sx; lim = LIM_X; }
   if (sy < s) { s = sy; lim = LIM_Y; }
   float dedx = 0.0f;
-  if constexpr (charged) {
+  if (charged) {
     dedx = tb.dedx[m];
     const float sl = (E > 1.0f) ? (LOSS_FRAC * E) / dedx : E / dedx;
     if (sl < s) { s = sl; lim = LIM_LOSS; }
@@ -184,7 +242,7 @@ __device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emi
   t.x = t.x + s * t.dx;
   t.y = t.y + s * t.dy;
   t.z = (lim == LIM_Z) ? zpl : (t.z + s * t.dz);
-  if constexpr (charged) {
+  if (charged) {
     const float beta = sqrtf(E * (E + TWO_MC2)) / (E + MC2);
     t.time = t.time + s / (beta * C_LIGHT);
   } else {
@@ -200,7 +258,7 @@ __device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emi
 
   // continuous loss, deposited in the pre-step slab
   float eout = E;
-  if constexpr (charged) {
+  if (charged) {
     const float de = (lim == LIM_LOSS && E <= 1.0f) ? E : dedx * s;
     eout = E - de;
     if (eout < 0.0f) eout = 0.0f;
@@ -223,133 +281,160 @@ __device__ __forceinline__ void step_track(Trk& t, const Tabs& tb, float log_emi
     escaped = true;
   }
 
-  int proc = PROC_NONE;
   if (escaped) {
-    o.esc = (double)eout;
+    o.esc = eout;
+    o.bal |= B_ESC;
     o.alive = 0;
     o.death = DEATH_ESCAPE;
   } else if (charged && eout < KC) {
-    o.cut = o.cut + (double)eout;
+    o.add_cut(eout);
     o.alive = 0;
     o.death = DEATH_CUT;
-    if constexpr (TYPE == EP) annihilate<MODE>(o, t, pstep, seed);
+    if (type == EP) annihilate<MODE>(o, t, pstep, seed);
   } else if (lim == LIM_PHYS) {
-    if constexpr (!charged) {
+    cx.E = E;
+    cx.sig = sig;
+    if (!charged) {
       const float4 cp = tb.cp[m * NBINS + bin];
-      const float sc = cp.x + f * cp.y;
-      const float sp = cp.z + f * cp.w;
-      const float r = u01(r0.y) * sig;
-      if (r < sc) {
-        // Compton (Butcher-Messel), attempt j on Philox block 1 + j, at most 64
-        proc = PROC_COMPTON;
-        const float k = E / MC2;
-        const float eps0 = 1.0f / (1.0f + 2.0f * k);
-        const float eps0sq = eps0 * eps0;
-        const float a1 = -m_log<MODE>(eps0);
-        const float a2 = 0.5f * (1.0f - eps0sq);
-        const float p1 = a1 / (a1 + a2);
-        float eps = 1.0f, epssq = 1.0f, onecost = 0.0f, sint2 = 0.0f;
-        int j;
-        for (j = 0; j < 64; ++j) {
-          const uint4 rj = philox(idlo, idhi, pstep, 1u + (uint32_t)j, seed, t.event);
-          const float ua = u01(rj.x), ub = u01(rj.y), uc = u01(rj.z);
-          if (p1 > ua) {
-            eps = m_exp<MODE>(-(a1 * ub));
-            epssq = eps * eps;
-          } else {
-            epssq = eps0sq + (1.0f - eps0sq) * ub;
-            eps = sqrtf(epssq);
-          }
-          onecost = (1.0f - eps) / (k * eps);
-          sint2 = onecost * (2.0f - onecost);
-          const float g = 1.0f - (eps * sint2) / (1.0f + epssq);
-          if (g >= uc) break;
-        }
-        if (j >= 64) o.reject = 1;
-        if (sint2 < 0.0f) sint2 = 0.0f;
-        const float cost = 1.0f - onecost;
-        const float sint = sqrtf(sint2);
-        float sphi, cphi;
-        m_sincos2pi<MODE>(u01(r0.w), &sphi, &cphi);
-        float nx, ny, nz;
-        rotate_about(t.dx, t.dy, t.dz, sint * cphi, sint * sphi, cost, nx, ny, nz);
-        const float e1 = eps * E;
-        const float te = E - e1;
-        if (te >= KC) {
-          const float px = E * t.dx - e1 * nx;
-          const float py = E * t.dy - e1 * ny;
-          const float pz = E * t.dz - e1 * nz;
-          const float pn = sqrtf(px * px + py * py + pz * pz);
-          add_sec(o, t, pstep, EM, te, px / pn, py / pn, pz / pn);
+      cx.sc = cp.x + f * cp.y;
+      cx.sp = cp.z + f * cp.w;
+    }
+    cx.u1 = u01(r0.y);
+    cx.u2 = u01(r0.z);
+    cx.u3 = u01(r0.w);
+    return true;
+  }
+  balance(t, E, o);
+  t.flags = (uint32_t)lim;
+  t.step = pstep + 1;
+  return false;
+}
+
+// The discrete interaction that ends a PHYS-limited step, then the step's balance.
+// t is the post-transport state (its step counter not yet advanced); o is fresh.
+template <int MODE>
+__device__ __forceinline__ void interact(const int type, Trk& t, const Ctx& cx, uint32_t seed,
+                                         StepOut& o) {
+  const bool charged = type != GAM;
+  o.begin();
+  o.dirty = D_POS | D_NIA | D_STEP | D_TIME | D_LEN | D_FLAGS | (charged ? D_E : 0u);
+  o.slab_cont = t.slab;
+  const uint32_t pstep = t.step;
+  const float E = cx.E;
+  int proc;
+  if (!charged) {
+    const float r = cx.u1 * cx.sig;
+    if (r < cx.sc) {
+      // Compton (Butcher-Messel), attempt j on Philox block 1 + j, at most 64
+      proc = PROC_COMPTON;
+      const uint32_t idlo = (uint32_t)t.id, idhi = (uint32_t)(t.id >> 32);
+      const float k = E / MC2;
+      const float eps0 = 1.0f / (1.0f + 2.0f * k);
+      const float eps0sq = eps0 * eps0;
+      const float a1 = -m_log<MODE>(eps0);
+      const float a2 = 0.5f * (1.0f - eps0sq);
+      const float p1 = a1 / (a1 + a2);
+      float eps = 1.0f, epssq = 1.0f, onecost = 0.0f, sint2 = 0.0f;
+      int j;
+      for (j = 0; j < 64; ++j) {
+        const uint4 rj = philox(idlo, idhi, pstep, 1u + (uint32_t)j, seed, t.event);
+        const float ua = u01(rj.x), ub = u01(rj.y), uc = u01(rj.z);
+        if (p1 > ua) {
+          eps = m_exp<MODE>(-(a1 * ub));
+          epssq = eps * eps;
         } else {
-          o.cut = o.cut + (double)te;
+          epssq = eps0sq + (1.0f - eps0sq) * ub;
+          eps = sqrtf(epssq);
         }
-        t.dx = nx;
-        t.dy = ny;
-        t.dz = nz;
-        t.e = e1;
-        o.dirty |= D_DIR | D_E;
-        if (!(e1 >= KC)) {
-          o.cut = o.cut + (double)e1;
-          o.alive = 0;
-          o.death = DEATH_CUT;
-        }
-      } else if (r < sc + sp && E > TWO_MC2) {
-        proc = PROC_PAIR;
-        const float avail = E - TWO_MC2;
-        const float em = u01(r0.z) * avail;
-        const float ep = avail - em;
-        o.mc = ((double)E - (double)em) - (double)ep;
-        if (em >= KC) add_sec(o, t, pstep, EM, em, t.dx, t.dy, t.dz);
-        else o.cut = o.cut + (double)em;
-        if (ep >= KC) {
-          add_sec(o, t, pstep, EP, ep, t.dx, t.dy, t.dz);
-        } else {
-          o.cut = o.cut + (double)ep;
-          annihilate<MODE>(o, t, pstep, seed);
-        }
-        o.alive = 0;
-        o.death = DEATH_ABSORB;
-      } else {
-        proc = PROC_PHOT;
-        if (E >= KC) add_sec(o, t, pstep, EM, E, t.dx, t.dy, t.dz);
-        else o.cut = o.cut + (double)E;
-        o.alive = 0;
-        o.death = DEATH_ABSORB;
+        onecost = (1.0f - eps) / (k * eps);
+        sint2 = onecost * (2.0f - onecost);
+        const float g = 1.0f - (eps * sint2) / (1.0f + epssq);
+        if (g >= uc) break;
       }
+      if (j >= 64) o.reject = 1;
+      if (sint2 < 0.0f) sint2 = 0.0f;
+      const float cost = 1.0f - onecost;
+      const float sint = sqrtf(sint2);
+      float sphi, cphi;
+      m_sincos2pi<MODE>(cx.u3, &sphi, &cphi);
+      float nx, ny, nz;
+      rotate_about(t.dx, t.dy, t.dz, sint * cphi, sint * sphi, cost, nx, ny, nz);
+      const float e1 = eps * E;
+      const float te = E - e1;
+      if (te >= KC) {
+        const float px = E * t.dx - e1 * nx;
+        const float py = E * t.dy - e1 * ny;
+        const float pz = E * t.dz - e1 * nz;
+        const float pn = sqrtf(px * px + py * py + pz * pz);
+        add_sec(o, EM, te, px / pn, py / pn, pz / pn);
+      } else {
+        o.add_cut(te);
+      }
+      t.dx = nx;
+      t.dy = ny;
+      t.dz = nz;
+      t.e = e1;
+      o.dirty |= D_DIR | D_E;
+      if (!(e1 >= KC)) {
+        o.add_cut(e1);
+        o.alive = 0;
+        o.death = DEATH_CUT;
+      }
+    } else if (r < cx.sc + cx.sp && E > TWO_MC2) {
+      proc = PROC_PAIR;
+      const float avail = E - TWO_MC2;
+      const float em = cx.u2 * avail;
+      const float ep = avail - em;
+      o.mc = ((double)E - (double)em) - (double)ep;
+      o.bal |= B_MC;
+      if (em >= KC) add_sec(o, EM, em, t.dx, t.dy, t.dz);
+      else o.add_cut(em);
+      if (ep >= KC) {
+        add_sec(o, EP, ep, t.dx, t.dy, t.dz);
+      } else {
+        o.add_cut(ep);
+        annihilate<MODE>(o, t, pstep, seed);
+      }
+      o.alive = 0;
+      o.death = DEATH_ABSORB;
     } else {
-      proc = PROC_BREM;
-      if (eout > KC) {
-        float kk = KC * m_exp<MODE>(u01(r0.z) * m_log<MODE>(eout / KC));
-        if (kk < KC) kk = KC;
-        if (kk > eout) kk = eout;
-        add_sec(o, t, pstep, GAM, kk, t.dx, t.dy, t.dz);
-        const float t2 = eout - kk;
-        t.e = t2;
-        if (t2 < KC) {
-          o.cut = o.cut + (double)t2;
-          o.alive = 0;
-          o.death = DEATH_CUT;
-          if constexpr (TYPE == EP) annihilate<MODE>(o, t, pstep, seed);
-        }
+      proc = PROC_PHOT;
+      if (E >= KC) add_sec(o, EM, E, t.dx, t.dy, t.dz);
+      else o.add_cut(E);
+      o.alive = 0;
+      o.death = DEATH_ABSORB;
+    }
+  } else {
+    // bremsstrahlung, 1/k spectrum on [k_c, T'] at the post-loss energy
+    proc = PROC_BREM;
+    const float eout = t.e;
+    if (eout > KC) {
+      float kk = KC * m_exp<MODE>(cx.u2 * m_log<MODE>(eout / KC));
+      if (kk < KC) kk = KC;
+      if (kk > eout) kk = eout;
+      add_sec(o, GAM, kk, t.dx, t.dy, t.dz);
+      const float t2 = eout - kk;
+      t.e = t2;
+      if (t2 < KC) {
+        o.add_cut(t2);
+        o.alive = 0;
+        o.death = DEATH_CUT;
+        if (type == EP) annihilate<MODE>(o, t, pstep, seed);
       }
     }
   }
-
-  // FP64 energy balance of the step, fixed order
-  double dep = (double)E;
-  dep = dep + o.mcr;
-  if (o.alive) dep = dep - (double)t.e;
-#pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (k < o.nsec) dep = dep - (double)o.sec(k).e;
-  dep = dep - o.esc;
-  dep = dep - o.cut;
-  dep = dep - o.mc;
-  o.dep = dep;
-
-  t.flags = (uint32_t)lim | ((uint32_t)proc << 4);
+  balance(t, E, o);
+  t.flags = (uint32_t)LIM_PHYS | ((uint32_t)proc << 4);
   t.step = pstep + 1;
+}
+
+// Both halves in sequence: exactly one step of the model.
+template <int MODE>
+__device__ __forceinline__ void step_track(const int type, Trk& t, const Tabs& tb, float log_emin,
+                                           float inv_dlog, float half, uint32_t seed, StepOut& o) {
+  Ctx cx;
+  if (transport<MODE>(type, t, tb, log_emin, inv_dlog, half, seed, o, cx))
+    interact<MODE>(type, t, cx, seed, o);
 }
 
 }  // namespace et

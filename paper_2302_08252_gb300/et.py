@@ -96,6 +96,8 @@ def _load():
         "et_set_timing": ([vp, C.c_int], st),
         "et_read_timing": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)], st),
         "et_debug_set_barrier_fault": ([vp, C.c_int, C.c_uint64], st),
+        "et_debug_iteration_times": ([vp, C.c_int], st),
+        "et_debug_read_iteration_times": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -315,6 +317,19 @@ def et_read_timing(ctx):
 
 def et_debug_set_barrier_fault(ctx, skip_block=-1, timeout_ns=0):
     _check(ctx, lib.et_debug_set_barrier_fault(ctx.handle, skip_block, timeout_ns))
+
+
+def et_debug_iteration_times(ctx, enable=True):
+    _check(ctx, lib.et_debug_iteration_times(ctx.handle, int(bool(enable))))
+
+
+def et_debug_read_iteration_times(ctx):
+    n = C.c_uint64()
+    _check(ctx, lib.et_debug_read_iteration_times(ctx.handle, None, 0, C.byref(n)))
+    out = np.zeros(n.value, dtype=np.uint64)
+    if n.value:
+        _check(ctx, lib.et_debug_read_iteration_times(ctx.handle, _p(out), n.value, C.byref(n)))
+    return out
 
 
 def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) -> Context:
