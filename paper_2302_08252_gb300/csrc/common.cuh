@@ -63,9 +63,14 @@ enum : uint32_t {
   D_ALL = (1u << NLEAF) - 1u,
 };
 
+// Count rows hold the types in the word order e-, gamma, e+ (then a pad word), so that
+// the e- and gamma counters are one aligned 64-bit word: a warp reserves room for both
+// (photon steps make electrons, electron steps make photons) with one atomic.
+__host__ __device__ constexpr int cw(int type) { return type == EM ? 0 : (type == GAM ? 1 : 2); }
+
 // ---- device control block (one per context) ----
-struct DevCtl {
-  uint32_t cnt[3][NTYPES];      // tracks per type; slot it%3 = current, (it+1)%3 = next
+struct alignas(16) DevCtl {
+  uint32_t cnt[3][4];          // tracks per type (word cw(t)); row it%3 current, (it+1)%3 next
   uint32_t iter;                // iteration about to run
   uint32_t status;              // ST_* bits
   uint32_t done;                // 1 when no track is left (graph driver)
@@ -74,7 +79,7 @@ struct DevCtl {
   unsigned long long steps[NTYPES];
   unsigned long long reject_cap_hits;
   unsigned long long idlog_n;
-  uint32_t hwm[NTYPES];         // sparse: slots handed out; dense: peak next fill
+  uint32_t hwm[4];              // word cw(t) -- sparse: slots handed out; dense: peak next fill
   uint32_t bar_count;           // grid barrier (persistent driver)
   uint32_t bar_gen;
   uint32_t free_top[NTYPES];    // sparse free-slot stacks (serving)
@@ -142,9 +147,62 @@ __device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
   return make_uint4(c0, c1, c2, c3);
 }
 
+// ---- exact conversions without the conversion instructions ----
+// On this GPU int<->float and float->double conversions and FRND issue to the FP64
+// pipe (2 lanes per cycle per SM), so the hot path builds the same values with integer
+// and FP32 operations instead.  Each function returns exactly what the named
+// conversion returns on its stated domain.
+
+// (float)v for an integer 0 <= v <= 2^24: the low 23 bits through the 2^23 magic
+// number (2^23 + lo - 2^23 == lo), the top bits added as exact powers of two.
+__device__ __forceinline__ float u24_to_float(uint32_t v) {
+  const float lo = __uint_as_float(0x4B000000u | (v & 0x7FFFFFu)) - 8388608.0f;
+  const uint32_t hi = v >> 23;  // 0, 1 or 2
+  return lo + (hi == 0u ? 0.0f : (hi == 1u ? 8388608.0f : 16777216.0f));
+}
+
+// rintf(y) (ties to even) and its integer value, for |y| < 2^22: adding 1.5 * 2^23 rounds
+// to an integer (ulp 1 in [2^23, 2^24)); the integer sits in the low mantissa bits.
+__device__ __forceinline__ float rint_small(float y, int& n) {
+  const float m = y + 12582912.0f;
+  n = __float_as_int(m) - 0x4B400000;
+  return m - 12582912.0f;
+}
+
+// floorf(y) and (int)floorf(y), for |y| < 2^22.
+__device__ __forceinline__ float floor_small(float y, int& n) {
+  float r = rint_small(y, n);
+  if (r > y) {
+    r = r - 1.0f;
+    n = n - 1;
+  }
+  return r;
+}
+
+// (float)e for a small integer |e| < 2^22.
+__device__ __forceinline__ float small_int_to_float(int e) {
+  return __int_as_float(0x4B400000 + e) - 12582912.0f;
+}
+
+// (double)x for a positive normal float: re-bias the exponent, widen the mantissa.
+__device__ __forceinline__ double pos_normal_to_double(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  const uint32_t m = u & 0x7FFFFFu;
+  return __hiloint2double((int)(((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// (double)x for any x >= +0 or -0 (energies): bit assembly for normal values, the
+// conversion instruction only for subnormals.
+__device__ __forceinline__ double f2d(float x) {
+  if (x >= 0x1p-126f) return pos_normal_to_double(x);
+  if (x == 0.0f) return __hiloint2double((int)(__float_as_uint(x) & 0x80000000u), 0);
+  return (double)x;
+}
+
 // (x >> 8) + 1 is at most 2^24, so both the conversion and the scaling are exact.
 __device__ __forceinline__ float u01(uint32_t x) {
-  return (float)((x >> 8) + 1u) * 0x1p-24f;
+  return u24_to_float((x >> 8) + 1u) * 0x1p-24f;
 }
 
 // SplitMix64 finalizer (Steele, Lea, Flood, OOPSLA 2014)
@@ -182,14 +240,15 @@ __device__ __forceinline__ float s_log(float x) {
   s = s * r2;
   const float t = r + r * s;
   const float lm = t + t;
-  const float fe = (float)e;
+  const float fe = small_int_to_float(e);
   return fe * 0x1.62e4p-1f + (lm + fe * 0x1.7f7d1cp-20f);
 }
 
 __device__ __forceinline__ float s_exp(float x) {
   if (x > 88.0f) return __uint_as_float(0x7f800000u);
   if (x < -87.0f) return 0.0f;
-  const float n = rintf(x * 0x1.715476p+0f);
+  int ni;
+  const float n = rint_small(x * 0x1.715476p+0f, ni);  // |x / ln2| < 128
   float r = x - n * 0x1.62e4p-1f;
   r = r - n * 0x1.7f7d1cp-20f;
   float p = 0x1.a01a02p-13f;          // 1/5040
@@ -200,13 +259,13 @@ __device__ __forceinline__ float s_exp(float x) {
   p = p * r + 0.5f;
   p = p * r + 1.0f;
   p = p * r + 1.0f;
-  const int ni = (int)n;
   return p * __uint_as_float((uint32_t)(ni + 127) << 23);
 }
 
 __device__ __forceinline__ void s_sincos2pi(float u, float* so, float* co) {
   const float v = 4.0f * u;
-  const float q = rintf(v);
+  int qi;
+  const float q = rint_small(v, qi);  // 0 <= v <= 4
   const float y = v - q;
   const float a = y * 0x1.921fb6p+0f;
   const float a2 = a * a;
@@ -222,7 +281,7 @@ __device__ __forceinline__ void s_sincos2pi(float u, float* so, float* co) {
   pc = pc * a2 - 0.5f;
   pc = pc * a2 + 1.0f;
   const float ca = pc;
-  const int k = ((int)q) & 3;
+  const int k = qi & 3;
   if (k == 0) { *so = sa; *co = ca; }
   else if (k == 1) { *so = ca; *co = -sa; }
   else if (k == 2) { *so = -sa; *co = -ca; }

@@ -443,7 +443,8 @@ static et_status one_hostloop_iteration(et_ctx* c, bool* empty) {
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   const uint32_t it = c->h_ctl->iter;
-  const uint32_t* n = c->h_ctl->cnt[it % 3];
+  const uint32_t* row = c->h_ctl->cnt[it % 3];
+  const uint32_t n[3] = {row[cw(EM)], row[cw(EP)], row[cw(GAM)]};
   *empty = (n[0] + n[1] + n[2]) == 0;
   if (*empty) return ET_OK;
   if (it >= c->cfg.max_iters) return fail(c, ET_ERR_CAPACITY, "iteration log full");
@@ -458,7 +459,7 @@ static void fill_stats(et_ctx* c, const DevCtl& before, et_iter_stats* out) {
   if (!out) return;
   const DevCtl& now = *c->h_ctl;
   const uint32_t cur = now.iter % 3;
-  for (int t = 0; t < 3; ++t) out->n_active[t] = now.cnt[cur][t];
+  for (int t = 0; t < 3; ++t) out->n_active[t] = now.cnt[cur][cw(t)];
   out->pad = 0;
   out->steps = 0;
   out->secondaries = 0;
@@ -697,7 +698,7 @@ et_status et_read_counters(et_ctx* c, et_counters* out) {
   for (int t = 0; t < 3; ++t) {
     out->steps[t] = d.steps[t];
     out->secondaries[t] = d.secondaries[t];
-    out->slot_high_water[t] = d.hwm[t];
+    out->slot_high_water[t] = d.hwm[cw(t)];
   }
   out->iterations = d.iter;
   out->reject_cap_hits = d.reject_cap_hits;

@@ -77,24 +77,40 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
   return v;
 }
 
-// Reserve per-type runs for a warp: returns the lane's first index per type.
-__device__ __forceinline__ void warp_reserve(uint32_t packed, uint32_t lane, uint32_t* counters,
+// Reserve per-type runs for a warp: returns the lane's first index per type.  `row` is a
+// count row in cw() word order: e- and gamma are reserved together by one 64-bit
+// atomicAdd (the counts never reach 2^32, so no carry crosses the halves), e+ by a
+// 32-bit one; a warp thus makes one atomic request in the common case.
+__device__ __forceinline__ void warp_reserve(uint32_t packed, uint32_t lane, uint32_t* row,
                                              uint32_t& p0, uint32_t& p1, uint32_t& p2) {
   const uint32_t incl = warp_incl_scan(packed, lane);
   const uint32_t total = __shfl_sync(FULL, incl, 31);
   const uint32_t excl = incl - packed;
-  uint32_t base = 0;
-  if (lane < 3) {
-    const uint32_t n = (total >> (10 * lane)) & 1023u;
-    if (n) base = atomicAdd(&counters[lane], n);
+  uint32_t b0 = 0, b1 = 0, b2 = 0;
+  if (lane == 0) {
+    const uint32_t ne = total & 1023u, np = (total >> 10) & 1023u, ng = (total >> 20) & 1023u;
+    if (ne | ng) {
+      const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(row),
+                                               (unsigned long long)ne | ((unsigned long long)ng << 32));
+      b0 = (uint32_t)old;
+      b2 = (uint32_t)(old >> 32);
+    }
+    if (np) b1 = atomicAdd(row + 2, np);
   }
-  p0 = __shfl_sync(FULL, base, 0) + (excl & 1023u);
-  p1 = __shfl_sync(FULL, base, 1) + ((excl >> 10) & 1023u);
-  p2 = __shfl_sync(FULL, base, 2) + ((excl >> 20) & 1023u);
+  p0 = __shfl_sync(FULL, b0, 0) + (excl & 1023u);
+  p1 = __shfl_sync(FULL, b1, 0) + ((excl >> 10) & 1023u);
+  p2 = __shfl_sync(FULL, b2, 0) + ((excl >> 20) & 1023u);
 }
 
-__device__ __forceinline__ uint32_t& pick(int ty, uint32_t& a0, uint32_t& a1, uint32_t& a2) {
-  return ty == 0 ? a0 : (ty == 1 ? a1 : a2);
+// Next position of the run of type ty, advanced by one.  Written with selects and
+// predicated increments: a reference to a dynamically chosen local would put the three
+// counters on the stack.
+__device__ __forceinline__ uint32_t take(int ty, uint32_t& a0, uint32_t& a1, uint32_t& a2) {
+  const uint32_t v = ty == 0 ? a0 : (ty == 1 ? a1 : a2);
+  a0 += (uint32_t)(ty == 0);
+  a1 += (uint32_t)(ty == 1);
+  a2 += (uint32_t)(ty == 2);
+  return v;
 }
 
 // Secondary k of a parent that has just taken its step (parent.step already advanced).
@@ -122,7 +138,7 @@ __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const St
       atomicAdd(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
       atomicAdd(&a.ledger[ev * 5 + 1], o.cut);
     }
-    if ((o.bal & B_ESC) && o.esc != 0.0f) atomicAdd(&a.ledger[ev * 5 + 2], (double)o.esc);
+    if ((o.bal & B_ESC) && o.esc != 0.0f) atomicAdd(&a.ledger[ev * 5 + 2], f2d(o.esc));
     if (o.bal & B_MCR) atomicAdd(&a.ledger[ev * 5 + 3], (double)MC2 + (double)MC2);
     if ((o.bal & B_MC) && o.mc != 0.0) atomicAdd(&a.ledger[ev * 5 + 4], o.mc);
   }
@@ -151,18 +167,28 @@ __device__ __forceinline__ void log_deaths(const Args& a, bool dead, const Trk& 
   }
 }
 
-// warp-aggregated per-type secondaries and reject-cap counters
-__device__ __forceinline__ void count_secondaries(const Args& a, uint32_t packed_sec, int reject,
-                                                  uint32_t lane) {
-  uint32_t v = packed_sec;
+// Per-lane tallies of secondaries per type and sampler-cap hits, kept in registers and
+// added to the control block once per warp and iteration (not once per chunk: those
+// counters are shared by every warp of the GPU).
+struct Tally {
+  uint32_t sec[3];
+  uint32_t rej;
+};
+
+__device__ __forceinline__ void tally_reset(Tally& tl) {
+  tl.sec[0] = tl.sec[1] = tl.sec[2] = 0;
+  tl.rej = 0;
+}
+
+__device__ __forceinline__ void tally_flush(const Args& a, Tally& tl, uint32_t lane) {
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
-  if (lane < 3) {
-    const uint32_t n = (v >> (10 * lane)) & 1023u;
-    if (n) atomicAdd(&a.ctl->secondaries[lane], (unsigned long long)n);
+  for (int t = 0; t < 3; ++t) {
+    const uint32_t n = __reduce_add_sync(FULL, tl.sec[t]);
+    if (lane == 0 && n) atomicAdd(&a.ctl->secondaries[t], (unsigned long long)n);
   }
-  const uint32_t rj = __ballot_sync(FULL, reject != 0);
-  if (rj && lane == 0) atomicAdd(&a.ctl->reject_cap_hits, (unsigned long long)__popc(rj));
+  const uint32_t r = __reduce_add_sync(FULL, tl.rej);
+  if (lane == 0 && r) atomicAdd(&a.ctl->reject_cap_hits, (unsigned long long)r);
+  tally_reset(tl);
 }
 
 // Pointer tables of the kernel arguments indexed by a run-time (warp-uniform) type:
@@ -276,7 +302,8 @@ __device__ __forceinline__ void q_get(const uint32_t* q, uint32_t s, Trk& t, Ctx
 // warp-uniform.
 template <int L, bool INSTR, bool DENSE>
 __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t it, uint32_t lane,
-                                       bool act, const Trk& t, const StepOut& o, uint32_t slot) {
+                                       bool act, const Trk& t, const StepOut& o, uint32_t slot,
+                                       Tally& tl) {
   const uint32_t hn = (it & 1u) ^ 1u;
   const uint32_t nslot = (it + 1) % 3;
   DevCtl* ctl = a.ctl;
@@ -288,17 +315,24 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
   // per-type record counts of this lane: survivor + secondaries
   uint32_t packed_sec = 0;
 #pragma unroll
-  for (int k = 0; k < 3; ++k)
-    if (k < nsec) packed_sec += 1u << (10 * o.type(k));
+  for (int k = 0; k < 3; ++k) {
+    if (k < nsec) {
+      const int ty = o.type(k);
+      packed_sec += 1u << (10 * ty);
+      tl.sec[0] += ty == 0;
+      tl.sec[1] += ty == 1;
+      tl.sec[2] += ty == 2;
+    }
+  }
   const uint32_t packed = (alive ? (1u << (10 * type)) : 0u) + packed_sec;
-  count_secondaries(a, packed_sec, act ? o.reject : 0, lane);
+  if (act) tl.rej += (uint32_t)o.reject;
 
   uint32_t q0, q1, q2;  // positions in the next arrays (dense) / next slot lists (sparse)
   warp_reserve(packed, lane, ctl->cnt[nslot], q0, q1, q2);
 
   if constexpr (DENSE) {
     if (alive) {
-      const uint32_t at = pick(type, q0, q1, q2)++;
+      const uint32_t at = take(type, q0, q1, q2);
       if (at < a.cap) view_of<L, INSTR>(a, type, (int)hn).store(at, t);
       else atomicOr(&ctl->status, ST_CAPACITY);
     }
@@ -306,7 +340,7 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
     for (int k = 0; k < 3; ++k) {
       if (k < nsec) {
         const int ty = o.type(k);
-        const uint32_t at = pick(ty, q0, q1, q2)++;
+        const uint32_t at = take(ty, q0, q1, q2);
         if (at < a.cap) view_of<L, INSTR>(a, ty, (int)hn).store(at, make_secondary(t, o.sec(k), k));
         else atomicOr(&ctl->status, ST_CAPACITY);
       }
@@ -317,7 +351,7 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
     warp_reserve(packed_sec, lane, ctl->hwm, s0, s1, s2);
     if (alive) {
       view_of<L, INSTR>(a, type, 0).store_leaves(slot, t, o.dirty);
-      const uint32_t at = pick(type, q0, q1, q2)++;
+      const uint32_t at = take(type, q0, q1, q2);
       if (at < a.cap) idx_of(a, type, (int)hn)[at] = slot;
       else atomicOr(&ctl->status, ST_CAPACITY);
     }
@@ -325,8 +359,8 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
     for (int k = 0; k < 3; ++k) {
       if (k < nsec) {
         const int ty = o.type(k);
-        const uint32_t ns = pick(ty, s0, s1, s2)++;
-        const uint32_t at = pick(ty, q0, q1, q2)++;
+        const uint32_t ns = take(ty, s0, s1, s2);
+        const uint32_t at = take(ty, q0, q1, q2);
         if (ns < a.cap && at < a.cap) {
           view_of<L, INSTR>(a, ty, 0).store(ns, make_secondary(t, o.sec(k), k));
           idx_of(a, ty, (int)hn)[at] = ns;
@@ -346,7 +380,7 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
 template <int MODE, int L, bool INSTR, bool DENSE>
 __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, const int type,
                                              uint32_t it, uint32_t i, bool valid, uint32_t lane,
-                                             WarpQueue& wq, bool drain_all) {
+                                             WarpQueue& wq, bool drain_all, Tally& tl) {
   const uint32_t hc = it & 1u;
   Trk t;
   StepOut o;
@@ -363,7 +397,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     }
     inter = transport<MODE>(type, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
   }
-  finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot);
+  finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot, tl);
   const uint32_t mask = __ballot_sync(FULL, inter);
   if (inter) {
     const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
@@ -381,7 +415,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
       interact<MODE>(type, t, cx, a.seed_lo, o);
     }
     __syncwarp();  // entries consumed before their ring slots are reused
-    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, qslot);
+    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, qslot, tl);
     wq.head = (wq.head + n) % QCAP;
     wq.count -= n;
   }
@@ -404,7 +438,7 @@ __global__ void __launch_bounds__(256) k_step(const __grid_constant__ Args a) {
   const DevCtl* ctl = a.ctl;
   if (ctl->status != 0) return;
   const uint32_t it = ctl->iter;
-  uint32_t n = ctl->cnt[it % 3][TYPE];
+  uint32_t n = ctl->cnt[it % 3][cw(TYPE)];
   n = n < a.cap ? n : a.cap;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -412,15 +446,18 @@ __global__ void __launch_bounds__(256) k_step(const __grid_constant__ Args a) {
   WarpQueue wq = warp_queue(smem, (int)a.n_mat);
   const uint32_t chunks = (n + 31u) / 32u;
   const bool batch = chunks >= 2u * nw;  // each warp sees several chunks: batching pays
+  Tally tl;
+  tally_reset(tl);
   uint32_t c = gw;
   while (c < chunks || wq.count) {
     const bool more = c < chunks;
     const uint32_t i = c * 32u + lane;
     const bool last = !more || c + nw >= chunks;
     process_warp<MODE, L, INSTR, DENSE>(a, tb, TYPE, it, i, more && i < n, lane, wq,
-                                        last || !batch);
+                                        last || !batch, tl);
     c += nw;
   }
+  tally_flush(a, tl, lane);
 }
 
 #ifdef ET_HOST_TU
@@ -431,10 +468,10 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
   const uint32_t it = c->iter;
   const uint32_t cur = it % 3, nxt = (it + 1) % 3;
   for (int t = 0; t < NTYPES; ++t) {
-    c->steps[t] += c->cnt[cur][t];
-    if (it < a.max_iters) a.counts_log[(size_t)it * 3 + t] = c->cnt[cur][t];
-    const uint32_t fill = c->cnt[nxt][t];
-    if (a.idx[0][0] == nullptr && fill > c->hwm[t]) c->hwm[t] = fill;  // dense: peak fill
+    c->steps[t] += c->cnt[cur][cw(t)];
+    if (it < a.max_iters) a.counts_log[(size_t)it * 3 + t] = c->cnt[cur][cw(t)];
+    const uint32_t fill = c->cnt[nxt][cw(t)];
+    if (a.idx[0][0] == nullptr && fill > c->hwm[cw(t)]) c->hwm[cw(t)] = fill;  // dense: peak fill
   }
   if (it >= a.max_iters) c->status |= ST_ITER_LOG_FULL;
   for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
@@ -513,10 +550,12 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
   const uint32_t stop_iter = *(volatile uint32_t*)&c->stop_iter;
   uint32_t status0 = *(volatile uint32_t*)&c->status;
   bool first = true;
+  Tally tl;  // flushed when the loop ends
+  tally_reset(tl);
   for (;;) {
     if (threadIdx.x == 0) {
       const uint32_t cur = it % 3;
-      for (int t = 0; t < 3; ++t) s_n[t] = __ldcg(&c->cnt[cur][t]);
+      for (int t = 0; t < 3; ++t) s_n[t] = __ldcg(&c->cnt[cur][cw(t)]);
       const uint32_t st = first ? status0 : *snap;
       s_stop = (s_n[0] + s_n[1] + s_n[2] == 0) || it >= stop_iter || st != 0;
     }
@@ -559,17 +598,18 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
         }
         // else: drain the previous type's queue first; this chunk is taken next round
       }
-      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, drain_all);
+      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, drain_all, tl);
     }
     if (!grid_sync(c, gridDim.x, a.timeout_ns, snap)) return;
     if (DENSE && blockIdx.x == 0 && threadIdx.x == 0) {
       for (int t = 0; t < 3; ++t) {
-        const uint32_t fill = __ldcg(&c->cnt[(it + 1) % 3][t]);
-        if (fill > c->hwm[t]) c->hwm[t] = fill;
+        const uint32_t fill = __ldcg(&c->cnt[(it + 1) % 3][cw(t)]);
+        if (fill > c->hwm[cw(t)]) c->hwm[cw(t)] = fill;
       }
     }
     ++it;
   }
+  tally_flush(a, tl, lane);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->iter = it;
     const uint32_t cur = it % 3;
@@ -630,7 +670,7 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
   warp_reserve(packed, lane, c->cnt[cur], q0, q1, q2);
   if (DENSE) {
     if (ok) {
-      const uint32_t at = pick(type, q0, q1, q2);
+      const uint32_t at = sel3(type, q0, q1, q2);
       if (at < a.cap) view_of<L, false>(a, type, (int)hc).store(at, t);
       else atomicOr(&c->status, ST_CAPACITY);
     }
@@ -638,8 +678,8 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
     uint32_t s0, s1, s2;
     warp_reserve(packed, lane, c->hwm, s0, s1, s2);
     if (ok) {
-      const uint32_t slot = pick(type, s0, s1, s2);
-      const uint32_t at = pick(type, q0, q1, q2);
+      const uint32_t slot = sel3(type, s0, s1, s2);
+      const uint32_t at = sel3(type, q0, q1, q2);
       if (slot < a.cap && at < a.cap) {
         view_of<L, false>(a, type, 0).store(slot, t);
         (hc ? a.idx[type][1] : a.idx[type][0])[at] = slot;

@@ -66,7 +66,7 @@ struct StepOut {
   __device__ __forceinline__ const Sec& sec(int k) const { return k == 0 ? s0 : (k == 1 ? s1 : s2); }
   __device__ __forceinline__ int type(int k) const { return (int)((types >> (2 * k)) & 3u); }
   __device__ __forceinline__ void add_cut(float x) {
-    cut = (bal & B_CUT) ? cut + (double)x : (double)x;  // 0 + x == x: same as summing from 0
+    cut = (bal & B_CUT) ? cut + f2d(x) : f2d(x);  // 0 + x == x: same as summing from 0
     bal |= B_CUT;
   }
   __device__ __forceinline__ void begin() {
@@ -158,16 +158,17 @@ __device__ __forceinline__ void balance(const Trk& t, float E, StepOut& o) {
     // arithmetic is needed on this, the common, path.
     const float e1 = t.e;
     o.dep_nz = e1 != E;
-    if (e1 >= 0.5f * E) o.dep = (double)(E - e1);
-    else o.dep = (double)E - (double)e1;
+    if (!o.dep_nz) o.dep = 0.0;                            // E - E = +0
+    else if (e1 >= 0.5f * E) o.dep = f2d(E - e1);          // exact difference
+    else o.dep = f2d(E) - f2d(e1);
   } else {
-    double dep = (double)E;
-    if (o.bal & B_MCR) dep = dep + ((double)MC2 + (double)MC2);
-    if (o.alive) dep = dep - (double)t.e;
+    double dep = f2d(E);
+    if (o.bal & B_MCR) dep = dep + (f2d(MC2) + f2d(MC2));
+    if (o.alive) dep = dep - f2d(t.e);
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      if (k < o.nsec) dep = dep - (double)o.sec(k).e;
-    if (o.bal & B_ESC) dep = dep - (double)o.esc;
+      if (k < o.nsec) dep = dep - f2d(o.sec(k).e);
+    if (o.bal & B_ESC) dep = dep - f2d(o.esc);
     if (o.bal & B_CUT) dep = dep - o.cut;
     if (o.bal & B_MC) dep = dep - o.mc;
     o.dep = dep;
@@ -195,11 +196,12 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
   // cross section at the pre-step energy
   const int s0 = t.slab;
   const int m = tb.mat[s0];
-  const float lx = (m_log<MODE>(E) - log_emin) * inv_dlog;
-  int bin = (int)floorf(lx);
-  bin = bin < 0 ? 0 : bin;
-  bin = bin > NBINS - 1 ? NBINS - 1 : bin;
-  const float f = lx - (float)bin;
+  const float lx = (m_log<MODE>(E) - log_emin) * inv_dlog;  // |lx| < 2^22 for any finite E > 0
+  int bin;
+  float fbin = floor_small(lx, bin);
+  if (bin < 0) { bin = 0; fbin = 0.0f; }
+  if (bin > NBINS - 1) { bin = NBINS - 1; fbin = (float)(NBINS - 1); }
+  const float f = lx - fbin;
   float sig;
   if (charged) {
     const float2 b = tb.brem[m * NBINS + bin];
@@ -385,7 +387,7 @@ __device__ __forceinline__ void interact(const int type, Trk& t, const Ctx& cx, 
       const float avail = E - TWO_MC2;
       const float em = cx.u2 * avail;
       const float ep = avail - em;
-      o.mc = ((double)E - (double)em) - (double)ep;
+      o.mc = (f2d(E) - f2d(em)) - f2d(ep);
       o.bal |= B_MC;
       if (em >= KC) add_sec(o, EM, em, t.dx, t.dy, t.dz);
       else o.add_cut(em);
