@@ -213,6 +213,49 @@ et_status et_reset(et_ctx* ctx);
 et_status et_set_timing(et_ctx* ctx, int on);
 et_status et_read_timing(et_ctx* ctx, double* ms_total, uint64_t* launches);
 
+/*
+ * Transport of one batch without any device allocation.  (The paper has no
+ * counterpart: this is a deployment convenience of this library.)
+ *
+ * For callers that cannot allocate device memory -- code running inside another
+ * framework's memory pool or under a budget that forbids cudaMalloc, code that must
+ * not synchronise the device (cudaMalloc/cudaFree may), plug-ins handed a stream and
+ * buffers but no allocator.  All scratch (dense double buffers of the three particle
+ * types, control block, iteration log, staged geometry and tables) lives in one
+ * file-scope device array of ET_NOALLOC_SCRATCH_BYTES, reserved when the library is
+ * loaded and held by every GPU that loads it until the process exits.  The call
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * Inputs: geometry and tables in host memory, as for et_create_geometry and
+ * et_load_tables (257 nodes per table); n_primaries records in device memory
+ * (16-byte aligned), validated on the device.  Outputs (device memory, zeroed and
+ * written by the call): score_device[n_events][n_slabs] per-slab deposits and
+ * ledger_device[n_events][5] = injected, below-cut, escaped, mass created, mass
+ * consumed (MeV).  steps_out (host, optional) receives the track steps taken.  The
+ * physics is the strict mode, run with the dense double buffer in AoS layout by the
+ * persistent kernel on `cuda_stream`; the call returns after the stream has finished.
+ *
+ * Limits: at most ET_NOALLOC_MAX_TRACKS active tracks per type in any iteration (and
+ * that many primaries), at most ET_NOALLOC_MAX_ITERS iterations; beyond either the
+ * call returns ET_ERR_CAPACITY with a message in err (err_len bytes, may be NULL).
+ *
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Every
+ * call shares the array and leaves its contents behind; a call clears what must start
+ * at zero.  Calls whose work overlaps on the GPU (different streams or host threads)
+ * race on the array.
+ */
+#define ET_NOALLOC_MAX_TRACKS 32768u
+#define ET_NOALLOC_MAX_ITERS 4096u
+#define ET_NOALLOC_SCRATCH_BYTES (13u << 20)
+et_status et_transport_noalloc(uint32_t n_slabs, const double* thickness_mm,
+                               const uint8_t* material, float half_xy_mm, uint32_t n_materials,
+                               float log_emin, float inv_dlog, const float* sigma,
+                               const float* dedx, const et_primary* primaries_device,
+                               size_t n_primaries, uint64_t seed, uint32_t n_events,
+                               double* score_device, double* ledger_device, uint64_t* steps_out,
+                               void* cuda_stream, char* err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

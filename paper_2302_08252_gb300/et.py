@@ -95,6 +95,9 @@ def _load():
         "et_reset": ([vp], st),
         "et_set_timing": ([vp, C.c_int], st),
         "et_read_timing": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)], st),
+        "et_transport_noalloc": ([C.c_uint32, vp, vp, C.c_float, C.c_uint32, C.c_float, C.c_float,
+                                  vp, vp, vp, C.c_size_t, C.c_uint64, C.c_uint32, vp, vp,
+                                  C.POINTER(C.c_uint64), vp, C.c_char_p, C.c_size_t], st),
         "et_debug_set_barrier_fault": ([vp, C.c_int, C.c_uint64], st),
         "et_debug_iteration_times": ([vp, C.c_int], st),
         "et_debug_read_iteration_times": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
@@ -330,6 +333,38 @@ def et_debug_read_iteration_times(ctx):
     if n.value:
         _check(ctx, lib.et_debug_read_iteration_times(ctx.handle, _p(out), n.value, C.byref(n)))
     return out
+
+
+NOALLOC_MAX_TRACKS = 32768
+NOALLOC_MAX_ITERS = 4096
+
+
+def et_transport_noalloc(geom, tables, primaries_device, n_primaries, seed, n_events,
+                         score_device, ledger_device, stream=None):
+    """The allocation-free transport of one batch (see et.h).  primaries_device: CUDA
+    tensor (or address) of n_primaries 48-byte records; score_device: CUDA float64
+    [n_events][n_slabs]; ledger_device: CUDA float64 [n_events][5].  Returns the steps."""
+    import torch
+    th = np.ascontiguousarray(geom["thickness"], dtype=np.float64)
+    mat = np.ascontiguousarray(geom["material"], dtype=np.uint8)
+    sig = np.ascontiguousarray(tables["sigma"], dtype=np.float32)
+    dedx = np.ascontiguousarray(tables["dedx"], dtype=np.float32)
+    addr = lambda x: x if isinstance(x, int) else x.data_ptr()
+    if stream is None:
+        s = torch.cuda.current_stream().cuda_stream
+    else:
+        s = stream if isinstance(stream, int) else stream.cuda_stream
+    steps = C.c_uint64()
+    err = C.create_string_buffer(256)
+    st = lib.et_transport_noalloc(len(th), _p(th), _p(mat), float(geom["half_xy"]), sig.shape[0],
+                                  float(tables["log_emin"]), float(tables["inv_dlog"]), _p(sig),
+                                  _p(dedx), C.c_void_p(addr(primaries_device)), n_primaries, seed,
+                                  n_events, C.c_void_p(addr(score_device)),
+                                  C.c_void_p(addr(ledger_device)), C.byref(steps), C.c_void_p(s),
+                                  err, len(err))
+    if st != ET_OK:
+        raise EtError(st, err.value.decode())
+    return steps.value
 
 
 def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) -> Context:
