@@ -373,14 +373,15 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
 }
 
 // One warp transports up to 32 tracks of one type (lanes with valid == false idle).
-// Lanes whose step ends in a discrete interaction go into the warp's queue; the
-// queue is drained 32 entries at a time, or completely when `drain_all` is set (end
-// of the warp's work in a type, or sparse iterations where batching cannot fill a
-// warp).  With no valid lane this call only drains.
+// With `batch` set, lanes whose step ends in a discrete interaction go into the warp's
+// queue, which is drained 32 entries at a time, or completely when `drain_all` is set
+// (the warp's last chunk of this type); a call with no valid lane only drains.
+// Without `batch` (iterations too small to fill a queue) the interactions run in place
+// and the whole chunk is finished in one pass: one slot reservation instead of two.
 template <int MODE, int L, bool INSTR, bool DENSE>
 __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, const int type,
                                              uint32_t it, uint32_t i, bool valid, uint32_t lane,
-                                             WarpQueue& wq, bool drain_all, Tally& tl) {
+                                             WarpQueue& wq, bool batch, bool drain_all, Tally& tl) {
   const uint32_t hc = it & 1u;
   Trk t;
   StepOut o;
@@ -397,27 +398,37 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     }
     inter = transport<MODE>(type, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
   }
-  finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot, tl);
-  const uint32_t mask = __ballot_sync(FULL, inter);
-  if (inter) {
-    const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
-    q_put(wq.q, pos, t, cx, slot);
-  }
-  wq.count += (uint32_t)__popc(mask);
-  __syncwarp();
-  while (wq.count >= 32u || (drain_all && wq.count)) {
-    // interactions of the n oldest entries, one per lane
-    const uint32_t n = wq.count >= 32u ? 32u : wq.count;
-    const bool act = lane < n;
-    uint32_t qslot = 0;
-    if (act) {
-      q_get(wq.q, (wq.head + lane) % QCAP, t, cx, qslot);
-      interact<MODE>(type, t, cx, a.seed_lo, o);
+  if (batch) {
+    finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot, tl);
+    const uint32_t mask = __ballot_sync(FULL, inter);
+    if (inter) {
+      const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
+      q_put(wq.q, pos, t, cx, slot);
     }
-    __syncwarp();  // entries consumed before their ring slots are reused
-    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, qslot, tl);
-    wq.head = (wq.head + n) % QCAP;
-    wq.count -= n;
+    wq.count += (uint32_t)__popc(mask);
+    __syncwarp();
+  }
+  bool once = !batch;
+  while (once || wq.count >= 32u || (drain_all && wq.count)) {
+    bool act, do_int;
+    uint32_t n = 0, s2 = slot;
+    if (once) {
+      act = valid;  // this chunk's own lanes, interactions in place
+      do_int = inter;
+    } else {
+      n = wq.count >= 32u ? 32u : wq.count;  // the n oldest queued entries, one per lane
+      act = lane < n;
+      do_int = act;
+      if (act) q_get(wq.q, (wq.head + lane) % QCAP, t, cx, s2);
+    }
+    if (do_int) interact<MODE>(type, t, cx, a.seed_lo, o);
+    if (!once) __syncwarp();  // entries consumed before their ring slots are reused
+    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, s2, tl);
+    if (!once) {
+      wq.head = (wq.head + n) % QCAP;
+      wq.count -= n;
+    }
+    once = false;
   }
 }
 
@@ -441,7 +452,9 @@ __global__ void __launch_bounds__(256) k_step(const __grid_constant__ Args a) {
   uint32_t n = ctl->cnt[it % 3][cw(TYPE)];
   n = n < a.cap ? n : a.cap;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // warps numbered block-first, so that the chunks of a small iteration land on
+  // different SMs instead of sharing the schedulers of the first few
+  const uint32_t gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   WarpQueue wq = warp_queue(smem, (int)a.n_mat);
   const uint32_t chunks = (n + 31u) / 32u;
@@ -453,8 +466,8 @@ __global__ void __launch_bounds__(256) k_step(const __grid_constant__ Args a) {
     const bool more = c < chunks;
     const uint32_t i = c * 32u + lane;
     const bool last = !more || c + nw >= chunks;
-    process_warp<MODE, L, INSTR, DENSE>(a, tb, TYPE, it, i, more && i < n, lane, wq,
-                                        last || !batch, tl);
+    process_warp<MODE, L, INSTR, DENSE>(a, tb, TYPE, it, i, more && i < n, lane, wq, batch,
+                                        last, tl);
     c += nw;
   }
   tally_flush(a, tl, lane);
@@ -543,7 +556,9 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
   DevCtl* c = a.ctl;
   uint32_t* snap = &c->status_snap;
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // warps numbered block-first, so that the chunks of a small iteration land on
+  // different SMs instead of sharing the schedulers of the first few
+  const uint32_t gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   if ((int)blockIdx.x == fault_skip_block) return;  // host-side fault injection: never arrives
   uint32_t it = *(volatile uint32_t*)&c->iter;
@@ -593,12 +608,12 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
           valid = i < nt;
           const uint32_t nxt = ch + nw;
           const int nty = nxt < wt ? (nxt < w0 ? EM : (nxt < w0 + w1 ? EP : GAM)) : -1;
-          drain_all = !batch || nty != ty;  // the warp's last chunk of this type
+          drain_all = nty != ty;  // the warp's last chunk of this type
           ch = nxt;
         }
         // else: drain the previous type's queue first; this chunk is taken next round
       }
-      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, drain_all, tl);
+      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, batch, drain_all, tl);
     }
     if (!grid_sync(c, gridDim.x, a.timeout_ns, snap)) return;
     if (DENSE && blockIdx.x == 0 && threadIdx.x == 0) {
