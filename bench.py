@@ -60,6 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-events", type=int, default=200)
     return ap.parse_args(argv)
 
 
@@ -269,6 +272,28 @@ def e2e_measure(et, ctx, prim, n_events, n_slabs, steps):
     return tot, secs, h2d, d2h
 
 
+def serving_measure(geom, args):
+    """Continuous batching under a Poisson stream of uneven events (1-1000 primaries of
+    mixed types, 0.1-100 GeV each): p50/p99 arrival-to-result latency and sustained
+    track-steps/s, tuned form and the plain sparse single buffer on the same stream."""
+    from paper_2302_08252_gb300 import serving
+    reqs = serving.poisson_requests(args.serving_rate, args.serving_events)
+    out = {"rate_per_s": args.serving_rate, "events": args.serving_events,
+           "event_sizes": "primaries per event log-uniform 1-1000, 0.1-100 GeV each"}
+    for name, form, layout, driver, cap in (("tuned", args.form, args.layout, args.driver, 22),
+                                            ("plain", "sparse", "aos", "hostloop", 24)):
+        srv = serving.Server(geom, form=form, layout=layout, driver=driver, capacity_log2=cap,
+                             max_events=max(1024, args.serving_events), iters_per_round=8)
+        st = srv.serve(reqs)
+        q = st.latency_quantiles()
+        out[name] = {"form": form, "layout": layout, "driver": driver,
+                     "p50_ms": 1e3 * q["p50"], "p99_ms": 1e3 * q["p99"],
+                     "steps_per_s": st.steps / st.wall, "wall_s": st.wall,
+                     "max_inflight": st.max_inflight, "rounds": st.rounds}
+        del srv
+    return out
+
+
 def cpu_baseline(geom, prim, n_events):
     import oracle
     cores = os.cpu_count() or 1
@@ -395,6 +420,8 @@ def ours_arm(args, rank, world, group):
             line["plain"] = {"value": pv, "unit": UNIT, "form": "sparse", "layout": "aos",
                              "driver": "hostloop", "steps": args.plain_steps}
             line["tuned_vs_plain"] = value / pv
+        if not args.no_serving:
+            line["serving"] = serving_measure(geom, args)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(geom, prim, n_events)
     line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)

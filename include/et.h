@@ -77,6 +77,10 @@ typedef struct {
   et_alloc_fn alloc;        /* optional; both or neither */
   et_free_fn free;
   void* alloc_user;
+  int32_t serving;          /* 1: count live tracks per event and report completed events
+                               (et_poll_completed), for continuous batching */
+  int32_t reuse_slots;      /* sparse form: 1 = slots of dead tracks are reused (from the next
+                               iteration on); 0 = never reused (the plain single buffer) */
 } et_config;
 
 /* Create a context (allocates the track buffers).  *out is NULL on failure. */
@@ -204,6 +208,18 @@ et_status et_read_counters(et_ctx* ctx, et_counters* out);
 
 /* Forget all tracks, scores, ledgers, logs and counters (buffers stay allocated). */
 et_status et_reset(et_ctx* ctx);
+
+/*
+ * Serving (cfg.serving): events whose last track died since the previous call, in the
+ * order they completed (at most cap; *n receives the number written).  An event is
+ * complete when the live-track count its injection raised returns to zero.  The call
+ * synchronises the context's stream.
+ */
+et_status et_poll_completed(et_ctx* ctx, uint32_t* events, uint64_t cap, uint64_t* n);
+
+/* Serving: clear an event's scores, ledger and live count so that its number can be
+ * given to a new event (call after reading its results). */
+et_status et_release_event(et_ctx* ctx, uint32_t event);
 
 /*
  * Timing of the step kernels (CUDA events on the context's stream around every

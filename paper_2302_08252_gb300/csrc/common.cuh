@@ -82,10 +82,23 @@ struct alignas(16) DevCtl {
   uint32_t hwm[4];              // word cw(t) -- sparse: slots handed out; dense: peak next fill
   uint32_t bar_count;           // grid barrier (persistent driver)
   uint32_t bar_gen;
-  uint32_t free_top[NTYPES];    // sparse free-slot stacks (serving)
   uint32_t status_snap;         // status as seen by the last grid barrier
-  uint32_t pad;
+  uint32_t n_done;              // serving: events completed so far (completion ring position)
+  // sparse slot reuse, per type (monotone counters; ring index = value % cap): slots in
+  // [free_head, free_snap) may be taken in this iteration, slots freed in this iteration
+  // are appended at free_tail and become takeable at the next iteration boundary
+  uint32_t free_head[4], free_tail[4], free_snap[4];  // word cw(t)
 };
+
+// Iteration boundary bookkeeping of the slot-reuse rings (one thread, all other
+// threads quiescent): heads that overshot the takeable range are pulled back, and the
+// slots freed in the iteration just ended become takeable.
+__device__ __forceinline__ void free_ring_boundary(DevCtl* c) {
+  for (int w = 0; w < 3; ++w) {
+    if ((int32_t)(c->free_head[w] - c->free_snap[w]) > 0) c->free_head[w] = c->free_snap[w];
+    c->free_snap[w] = c->free_tail[w];
+  }
+}
 
 struct IdRec {
   unsigned long long id;
@@ -121,6 +134,13 @@ struct Args {
   uint32_t* heat[NTYPES][2];    // per-word access counts or NULL
   unsigned long long timeout_ns;// bounded waits (persistent driver)
   unsigned long long* iter_ns;  // persistent driver: %globaltimer at each iteration start, or NULL
+  // serving: live tracks per event; an event whose count returns to zero is appended to
+  // the completion ring (NULL: off)
+  int32_t* live;                // [max_events]
+  uint32_t* done_ring;          // [done_cap] completed event ids, position n_done % done_cap
+  uint32_t done_cap;
+  // sparse form with slot reuse: ring of freed slots per type (NULL: slots never reused)
+  uint32_t* free_ring[NTYPES];  // [cap] each
 };
 
 constexpr int MAX_SLABS = 128;

@@ -62,6 +62,7 @@ struct et_ctx {
   uint64_t launches = 0;
   int fault_skip_block = -1;  // fault injection for the persistent driver's barrier (tests)
   unsigned long long* d_iter_ns = nullptr;
+  uint32_t done_read = 0;     // serving: completion ring entries already returned
 };
 
 static et_status fail(et_ctx* c, et_status s, const char* fmt, ...) {
@@ -220,6 +221,18 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
     if (!a.idlog) return fail(c, ET_ERR_NOMEM, "id log");
     a.idlog_cap = k.id_log_capacity;
   }
+  if (k.serving) {
+    a.live = (int32_t*)dalloc(c, (size_t)k.max_events * 4u);
+    a.done_ring = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
+    a.done_cap = k.max_events;
+    if (!a.live || !a.done_ring) return fail(c, ET_ERR_NOMEM, "serving counters");
+  }
+  if (k.reuse_slots && !c->dense) {
+    for (int t = 0; t < 3; ++t) {
+      a.free_ring[t] = (uint32_t*)dalloc(c, (size_t)c->cap * 4u);
+      if (!a.free_ring[t]) return fail(c, ET_ERR_NOMEM, "free-slot ring");
+    }
+  }
   a.seed_lo = (uint32_t)k.seed;
   a.timeout_ns = 2000000000ull;
   if (cudaMallocHost(&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
@@ -259,6 +272,8 @@ et_status et_reset(et_ctx* c) {
   if (a.score)
     CUDA_TRY(c, cudaMemsetAsync(a.score, 0, (size_t)a.max_events * a.n_slabs * 8u, c->stream));
   if (a.trace) CUDA_TRY(c, cudaMemsetAsync(a.trace, 0, 3u * NLEAF * 2u * 8u, c->stream));
+  if (a.live) CUDA_TRY(c, cudaMemsetAsync(a.live, 0, (size_t)a.max_events * 4u, c->stream));
+  c->done_read = 0;
   for (int t = 0; t < 3; ++t)
     for (int h = 0; h < 2; ++h)
       if (a.heat[t][h])
@@ -704,6 +719,42 @@ et_status et_read_counters(et_ctx* c, et_counters* out) {
   out->reject_cap_hits = d.reject_cap_hits;
   out->kernel_launches = c->launches;
   out->status = d.status;
+  return ET_OK;
+}
+
+et_status et_poll_completed(et_ctx* c, uint32_t* events, uint64_t cap, uint64_t* n) {
+  if (!c || !n) return ET_ERR_INVALID;
+  if (!c->args.live) return fail(c, ET_ERR_STATE, "not a serving context");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const uint32_t done = c->h_ctl->n_done;
+  uint32_t avail = done - c->done_read;
+  if (avail > c->args.done_cap) return fail(c, ET_ERR_CAPACITY, "completion ring overrun");
+  if (avail > cap) avail = (uint32_t)cap;
+  *n = avail;
+  if (!avail) return ET_OK;
+  if (!events) return fail(c, ET_ERR_INVALID, "no output buffer");
+  const uint32_t dc = c->args.done_cap;
+  const uint32_t first = c->done_read % dc;
+  const uint32_t n1 = avail < dc - first ? avail : dc - first;
+  CUDA_TRY(c, cudaMemcpyAsync(events, c->args.done_ring + first, (size_t)n1 * 4u,
+                              cudaMemcpyDeviceToHost, c->stream));
+  if (n1 < avail)
+    CUDA_TRY(c, cudaMemcpyAsync(events + n1, c->args.done_ring, (size_t)(avail - n1) * 4u,
+                                cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->done_read += avail;
+  return ET_OK;
+}
+
+et_status et_release_event(et_ctx* c, uint32_t event) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->have_geom) return fail(c, ET_ERR_STATE, "no geometry");
+  if (event >= c->cfg.max_events) return fail(c, ET_ERR_INVALID, "bad event");
+  const size_t ns = c->args.n_slabs;
+  CUDA_TRY(c, cudaMemsetAsync(c->args.score + (size_t)event * ns, 0, ns * 8u, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->args.ledger + (size_t)event * 5u, 0, 5u * 8u, c->stream));
+  if (c->args.live) CUDA_TRY(c, cudaMemsetAsync(c->args.live + event, 0, 4u, c->stream));
   return ET_OK;
 }
 

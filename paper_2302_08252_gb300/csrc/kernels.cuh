@@ -113,6 +113,57 @@ __device__ __forceinline__ uint32_t take(int ty, uint32_t& a0, uint32_t& a1, uin
   return v;
 }
 
+// Sparse form: slots for a warp's new tracks.  Per type, the warp's run of k positions is
+// made of `got` reused slots (the ring entries from `ring_base`) followed by fresh slots
+// from the high-water counter (from `fresh`); each lane walks its own positions `pos`.
+struct SlotRuns {
+  uint32_t ring_base[3], got[3], fresh[3];
+  uint32_t pos0, pos1, pos2;
+};
+
+template <typename T>
+__device__ __forceinline__ T sel3(int ty, T v0, T v1, T v2);
+
+__device__ __forceinline__ void sparse_reserve(const Args& a, uint32_t packed, uint32_t lane,
+                                               SlotRuns& sr) {
+  DevCtl* c = a.ctl;
+  const uint32_t incl = warp_incl_scan(packed, lane);
+  const uint32_t total = __shfl_sync(FULL, incl, 31);
+  const uint32_t excl = incl - packed;
+  const bool reuse = a.free_ring[0] != nullptr;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    uint32_t rb = 0, got = 0, fresh = 0;
+    const uint32_t k = (total >> (10 * t)) & 1023u;
+    if (lane == 0 && k) {
+      if (reuse) {
+        rb = atomicAdd(&c->free_head[cw(t)], k);
+        const int avail = (int)(__ldcg(&c->free_snap[cw(t)]) - rb);
+        got = avail <= 0 ? 0u : (avail < (int)k ? (uint32_t)avail : k);
+      }
+      if (k > got) fresh = atomicAdd(&c->hwm[cw(t)], k - got);
+    }
+    sr.ring_base[t] = __shfl_sync(FULL, rb, 0);
+    sr.got[t] = __shfl_sync(FULL, got, 0);
+    sr.fresh[t] = __shfl_sync(FULL, fresh, 0);
+  }
+  sr.pos0 = excl & 1023u;
+  sr.pos1 = (excl >> 10) & 1023u;
+  sr.pos2 = (excl >> 20) & 1023u;
+}
+
+// The lane's next slot of type ty.
+__device__ __forceinline__ uint32_t sparse_slot(const Args& a, SlotRuns& sr, int ty) {
+  const uint32_t p = take(ty, sr.pos0, sr.pos1, sr.pos2);
+  const uint32_t got = sel3(ty, sr.got[0], sr.got[1], sr.got[2]);
+  if (p < got) {
+    const uint32_t* ring = sel3(ty, a.free_ring[0], a.free_ring[1], a.free_ring[2]);
+    return __ldcg(ring + ((sel3(ty, sr.ring_base[0], sr.ring_base[1], sr.ring_base[2]) + p) &
+                          (a.cap - 1u)));
+  }
+  return sel3(ty, sr.fresh[0], sr.fresh[1], sr.fresh[2]) + (p - got);
+}
+
 // Secondary k of a parent that has just taken its step (parent.step already advanced).
 __device__ __forceinline__ Trk make_secondary(const Trk& parent, const Sec& s, int k) {
   Trk r;
@@ -346,9 +397,9 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
       }
     }
   } else {
-    // fresh slots for the secondaries
-    uint32_t s0, s1, s2;
-    warp_reserve(packed_sec, lane, ctl->hwm, s0, s1, s2);
+    // slots for the secondaries: reused ones first (when enabled), then fresh ones
+    SlotRuns sr;
+    sparse_reserve(a, packed_sec, lane, sr);
     if (alive) {
       view_of<L, INSTR>(a, type, 0).store_leaves(slot, t, o.dirty);
       const uint32_t at = take(type, q0, q1, q2);
@@ -359,7 +410,7 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
     for (int k = 0; k < 3; ++k) {
       if (k < nsec) {
         const int ty = o.type(k);
-        const uint32_t ns = take(ty, s0, s1, s2);
+        const uint32_t ns = sparse_slot(a, sr, ty);
         const uint32_t at = take(ty, q0, q1, q2);
         if (ns < a.cap && at < a.cap) {
           view_of<L, INSTR>(a, ty, 0).store(ns, make_secondary(t, o.sec(k), k));
@@ -367,6 +418,30 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
         } else {
           atomicOr(&ctl->status, ST_CAPACITY);
         }
+      }
+    }
+    // the slot of a track that died becomes reusable at the next iteration boundary
+    if (a.free_ring[0]) {
+      const bool freed = act && !o.alive;
+      const uint32_t m = __ballot_sync(FULL, freed);
+      if (m) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&ctl->free_tail[cw(type)], (uint32_t)__popc(m));
+        base = __shfl_sync(FULL, base, 0);
+        if (freed)
+          sel3(type, a.free_ring[0], a.free_ring[1], a.free_ring[2])
+              [(base + __popc(m & ((1u << lane) - 1u))) & (a.cap - 1u)] = slot;
+      }
+    }
+  }
+  // serving: live-track count of the event; the step that brings it to zero ends the event
+  if (a.live && act) {
+    const int delta = (o.alive ? 1 : 0) + nsec - 1;
+    if (delta != 0) {
+      const int old = atomicAdd(&a.live[t.event], delta);
+      if (old + delta == 0) {
+        const uint32_t pos = atomicAdd(&ctl->n_done, 1u);
+        a.done_ring[pos % a.done_cap] = t.event;
       }
     }
   }
@@ -487,6 +562,7 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
     if (a.idx[0][0] == nullptr && fill > c->hwm[cw(t)]) c->hwm[cw(t)] = fill;  // dense: peak fill
   }
   if (it >= a.max_iters) c->status |= ST_ITER_LOG_FULL;
+  free_ring_boundary(c);
   for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
   c->iter = it + 1;
   const uint32_t left = c->cnt[nxt][0] + c->cnt[nxt][1] + c->cnt[nxt][2];
@@ -519,6 +595,7 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
     if (arrived == nblocks - 1) {
       cnt.store(0u, cuda::memory_order_relaxed);
       *snap_status = st.load(cuda::memory_order_relaxed);
+      free_ring_boundary(c);  // every other block is waiting here: no slot is being taken
       gen.store(g + 1u, cuda::memory_order_release);
     } else {
       const unsigned long long t0 = global_ns();
@@ -556,9 +633,11 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
   DevCtl* c = a.ctl;
   uint32_t* snap = &c->status_snap;
   const uint32_t lane = threadIdx.x & 31u;
-  // warps numbered block-first, so that the chunks of a small iteration land on
-  // different SMs instead of sharing the schedulers of the first few
-  const uint32_t gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  // two warp numberings: block-major for large iterations; block-first for small ones, so
+  // that their few chunks land on different SMs instead of sharing the schedulers of
+  // the first few
+  const uint32_t gw_major = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t gw_spread = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   if ((int)blockIdx.x == fault_skip_block) return;  // host-side fault injection: never arrives
   uint32_t it = *(volatile uint32_t*)&c->iter;
@@ -592,7 +671,7 @@ __global__ void __launch_bounds__(256, 2) k_persistent(const __grid_constant__ A
     // static chunk order: warp w takes chunks w, w + nw, ...; the type changes at most
     // twice per warp and iteration, and the queue is emptied at each change
     const bool batch = wt >= 2u * nw;  // each warp sees several chunks: batching pays
-    uint32_t ch = gw;
+    uint32_t ch = batch ? gw_major : gw_spread;
     int qtype = EM;
     while (ch < wt || wq.count) {
       int ty = qtype;
@@ -679,6 +758,7 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
     t.len = 0.0f;
     t.flags = 0;
     atomicAdd(&a.ledger[(size_t)t.event * 5 + 0], (double)t.e);
+    if (a.live) atomicAdd(&a.live[t.event], 1);
   }
   const uint32_t packed = ok ? (1u << (10 * type)) : 0u;
   uint32_t q0, q1, q2;
@@ -690,10 +770,10 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
       else atomicOr(&c->status, ST_CAPACITY);
     }
   } else {
-    uint32_t s0, s1, s2;
-    warp_reserve(packed, lane, c->hwm, s0, s1, s2);
+    SlotRuns sr;
+    sparse_reserve(a, packed, lane, sr);
     if (ok) {
-      const uint32_t slot = sel3(type, s0, s1, s2);
+      const uint32_t slot = sparse_slot(a, sr, type);
       const uint32_t at = sel3(type, q0, q1, q2);
       if (slot < a.cap && at < a.cap) {
         view_of<L, false>(a, type, 0).store(slot, t);

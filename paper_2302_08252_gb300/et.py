@@ -49,7 +49,8 @@ class et_config(C.Structure):
                 ("seed", C.c_uint64), ("max_events", C.c_uint32), ("max_iters", C.c_uint32),
                 ("instrument", C.c_int32), ("id_log", C.c_int32),
                 ("id_log_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("serving", C.c_int32), ("reuse_slots", C.c_int32)]
 
 
 class et_iter_stats(C.Structure):
@@ -93,6 +94,8 @@ def _load():
         "et_read_heatmap": ([vp, C.c_uint32, C.c_uint32, vp, C.c_uint64], st),
         "et_read_counters": ([vp, C.POINTER(et_counters)], st),
         "et_reset": ([vp], st),
+        "et_poll_completed": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
+        "et_release_event": ([vp, C.c_uint32], st),
         "et_set_timing": ([vp, C.c_int], st),
         "et_read_timing": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)], st),
         "et_transport_noalloc": ([C.c_uint32, vp, vp, C.c_float, C.c_uint32, C.c_float, C.c_float,
@@ -154,7 +157,7 @@ def _torch_callbacks():
 def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_STRICT,
               driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
               instrument=False, id_log=False, id_log_capacity=0, stream=None,
-              use_torch_allocator=True) -> Context:
+              use_torch_allocator=True, serving=False, reuse_slots=False) -> Context:
     """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
     torch's current stream."""
     import torch
@@ -180,6 +183,8 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
     cfg.id_log = int(bool(id_log))
     cfg.id_log_capacity = id_log_capacity
     cfg.cuda_stream = s
+    cfg.serving = int(bool(serving))
+    cfg.reuse_slots = int(bool(reuse_slots))
     cbs = None
     if use_torch_allocator:
         cbs = _torch_callbacks()
@@ -305,6 +310,17 @@ def et_read_counters(ctx):
 
 def et_reset(ctx):
     _check(ctx, lib.et_reset(ctx.handle))
+
+
+def et_poll_completed(ctx, cap=1 << 16):
+    out = np.zeros(cap, dtype=np.uint32)
+    n = C.c_uint64()
+    _check(ctx, lib.et_poll_completed(ctx.handle, _p(out), cap, C.byref(n)))
+    return out[: n.value].copy()
+
+
+def et_release_event(ctx, event):
+    _check(ctx, lib.et_release_event(ctx.handle, event))
 
 
 def et_set_timing(ctx, on=True):

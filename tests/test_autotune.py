@@ -1,0 +1,47 @@
+"""Autotuner: selection logic and sampling on CPU; on the GPU, tuning a batched workload of
+uneven events and checking that the chosen configuration reproduces the oracle."""
+import numpy as np
+import pytest
+
+from paper_2302_08252_gb300 import autotune
+from paper_2302_08252_gb300 import workloads as W
+
+
+def test_selection_picks_fastest_and_covers_all_candidates():
+    cost = {"aos": 3.0, "soa": 2.0, "aosoa32": 1.0, "aosoa64": 1.5}
+    timer = lambda layout, block, driver: cost[layout] + {64: 0.3, 128: 0.1, 256: 0.2}[block] + \
+        {"persistent": 0.0, "graph": 1.0, "hostloop": 2.0}[driver]
+    r = autotune.autotune(None, W.uneven_events(8, 5), 8, timer=timer)
+    assert len(r["table"]) == 4 * 3 * 3
+    assert r["best"]["layout"] == "aosoa32" and r["best"]["block_size"] == 128
+    assert r["best"]["driver"] == "persistent"
+
+
+def test_sampling_keeps_event_numbers():
+    p = W.uneven_events(64, 20)
+    s = autotune.sample_events(p, 10)
+    assert len(np.unique(s["event"])) == 10
+    for e in np.unique(s["event"]):
+        assert np.array_equal(s[s["event"] == e]["id"], p[p["event"] == e]["id"])
+
+
+def test_cache(tmp_path):
+    calls = []
+    f = lambda: calls.append(1) or {"x": 1}
+    path = str(tmp_path / "tune.json")
+    assert autotune.cached(path, "k", f) == {"x": 1}
+    assert autotune.cached(path, "k", f) == {"x": 1}
+    assert len(calls) == 1
+
+
+@pytest.mark.gpu
+def test_autotuned_batched_run_matches_oracle(geom):
+    from parity import assert_strict_parity, oracle_run, run_gpu
+    p = W.uneven_events(24, 6)
+    p["ekin"] = np.minimum(p["ekin"], np.float32(2000.0))
+    r = autotune.autotune(geom, p, 24, layouts=("aos", "aosoa32"), blocks=(128, 256),
+                          drivers=("persistent", "graph"), reps=1, capacity_log2=18)
+    b = r["best"]
+    g = run_gpu(geom, p, 24, form="dense", layout=b["layout"], driver=b["driver"],
+                block_size=b["block_size"], capacity_log2=18)
+    assert_strict_parity(g, oracle_run(geom, p, 24))
