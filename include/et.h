@@ -118,6 +118,14 @@ et_status et_load_tables(et_ctx* ctx, uint32_t n_materials, uint32_t n_nodes, fl
 et_status et_build_toy_tables(uint32_t n_materials, uint32_t n_nodes, float* sigma_out,
                               float* dedx_out, float* log_emin_out, float* inv_dlog_out);
 
+/*
+ * The same closed forms, not rounded: FP64 nodes for the all-FP64 build below.
+ * sigma_out[n_materials][5][n_nodes], dedx_out[n_materials]; log_emin_out and
+ * inv_dlog_out (optional) receive ln(1e-3 MeV) and (n_nodes - 1) / ln(1e8).
+ */
+et_status et_build_toy_tables_fp64(uint32_t n_materials, uint32_t n_nodes, double* sigma_out,
+                                   double* dedx_out, double* log_emin_out, double* inv_dlog_out);
+
 /* A primary particle (48 bytes). */
 typedef struct {
   uint32_t type;   /* ET_EMINUS, ET_EPLUS, ET_GAMMA */
@@ -271,6 +279,36 @@ et_status et_transport_noalloc(uint32_t n_slabs, const double* thickness_mm,
                                size_t n_primaries, uint64_t seed, uint32_t n_events,
                                double* score_device, double* ledger_device, uint64_t* steps_out,
                                void* cuda_stream, char* err, size_t err_len);
+
+/*
+ * All-FP64 transport (the precision comparison of the mixed-primary workload, which
+ * sets the FP32-stepping path against a build where state, tables and arithmetic are
+ * all FP64): the toy model of the strict mode with every REAL in FP64 and
+ * libm-accuracy log, exp, sin and cos, i.e. the GPU counterpart of the FP64 reference
+ * model, not a bit-exact mirror of it (CUDA's and the C library's log/exp may differ
+ * in the last bit).  Iterations as in Sec. 2 (each active track advances one step;
+ * survivors and secondaries form the next iteration), dense double buffer of 128-byte
+ * AoS records, one step kernel per particle type, launched from the host until no
+ * track is left.  A plain path: it allocates its buffers (cudaMalloc) per call and
+ * returns only when the run is over.
+ *
+ * Inputs (host memory): geometry as for et_create_geometry; FP64 tables
+ * sigma[n_materials][5][257] in the node layout of et_load_tables, dedx[n_materials];
+ * n primaries; 2^capacity_log2 (6..26) slots per type and buffer.  Outputs (host
+ * memory): score_out[n_events][n_slabs] per-slab deposits, ledger_out[n_events][5]
+ * (optional) as for et_transport_noalloc, steps_out and iterations_out (optional).
+ * Errors: ET_ERR_INVALID for bad arguments or primaries (type, event >= n_events,
+ * ekin <= 0, z outside the slabs); ET_ERR_CAPACITY if the primaries or a buffer
+ * exceed the capacity; ET_ERR_TIMEOUT after 65536 iterations with tracks left;
+ * ET_ERR_NOMEM / ET_ERR_CUDA from the runtime.  Uses the current device's default
+ * stream.
+ */
+et_status et_run_fp64(uint32_t n_slabs, const double* thickness_mm, const uint8_t* material,
+                      double half_xy_mm, uint32_t n_materials, double log_emin, double inv_dlog,
+                      const double* sigma, const double* dedx, const et_primary* primaries,
+                      size_t n, uint64_t seed, uint32_t n_events, uint32_t capacity_log2,
+                      double* score_out, double* ledger_out, uint64_t* steps_out,
+                      uint64_t* iterations_out);
 
 #ifdef __cplusplus
 }

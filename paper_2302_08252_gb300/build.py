@@ -60,6 +60,8 @@ def _jobs():
                  os.path.join(OUT, "et_api.o")])
     jobs.append([_nvcc(), *COMMON, *STRICT, "-c", os.path.join(CSRC, "noalloc.cu"), "-o",
                  os.path.join(OUT, "noalloc.o")])
+    jobs.append([_nvcc(), *COMMON, *STRICT, "-c", os.path.join(CSRC, "fp64.cu"), "-o",
+                 os.path.join(OUT, "fp64.o")])
     jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-I", INC, "-c",
                  os.path.join(CSRC, "toy_tables.cpp"), "-o", os.path.join(OUT, "toy_tables.o")])
     return jobs

@@ -65,6 +65,30 @@ double brems(const Medium& m, double t) {
 
 }  // namespace
 
+extern "C" et_status et_build_toy_tables_fp64(uint32_t n_materials, uint32_t n_nodes,
+                                              double* sigma_out, double* dedx_out,
+                                              double* log_emin_out, double* inv_dlog_out) {
+  if (n_materials < 1 || n_materials > 2 || n_nodes < 2 || !sigma_out || !dedx_out)
+    return ET_ERR_INVALID;
+  for (uint32_t m = 0; m < n_materials; ++m) {
+    const Medium& md = kMedia[m];
+    double* row = sigma_out + (size_t)m * 5 * n_nodes;
+    for (uint32_t i = 0; i < n_nodes; ++i) {
+      const double e = 1e-3 * std::pow(10.0, 8.0 * (double)i / (double)(n_nodes - 1));
+      const double c = compton(md, e), p = pair(md, e), f = photo(md, e);
+      row[0 * n_nodes + i] = c;
+      row[1 * n_nodes + i] = p;
+      row[2 * n_nodes + i] = f;
+      row[3 * n_nodes + i] = c + p + f;
+      row[4 * n_nodes + i] = brems(md, e);
+    }
+    dedx_out[m] = md.stopping;
+  }
+  if (log_emin_out) *log_emin_out = std::log(1e-3);
+  if (inv_dlog_out) *inv_dlog_out = (double)(n_nodes - 1) / std::log(1e8);
+  return ET_OK;
+}
+
 extern "C" et_status et_build_toy_tables(uint32_t n_materials, uint32_t n_nodes, float* sigma_out,
                                          float* dedx_out, float* log_emin_out, float* inv_dlog_out) {
   if (n_materials < 1 || n_materials > 2 || n_nodes < 2 || !sigma_out || !dedx_out)

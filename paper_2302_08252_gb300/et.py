@@ -82,6 +82,10 @@ def _load():
         "et_create_geometry": ([vp, C.c_uint32, vp, vp, C.c_float], st),
         "et_load_tables": ([vp, C.c_uint32, C.c_uint32, C.c_float, C.c_float, vp, vp], st),
         "et_build_toy_tables": ([C.c_uint32, C.c_uint32, vp, vp, vp, vp], st),
+        "et_build_toy_tables_fp64": ([C.c_uint32, C.c_uint32, vp, vp, vp, vp], st),
+        "et_run_fp64": ([C.c_uint32, vp, vp, C.c_double, C.c_uint32, C.c_double, C.c_double, vp,
+                         vp, vp, C.c_size_t, C.c_uint64, C.c_uint32, C.c_uint32, vp, vp,
+                         C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], st),
         "et_inject": ([vp, vp, C.c_size_t], st),
         "et_inject_device": ([vp, vp, C.c_size_t], st),
         "et_run_iteration": ([vp, C.POINTER(et_iter_stats)], st),
@@ -218,6 +222,17 @@ def et_build_toy_tables(n_materials=2, n_nodes=257):
     st = lib.et_build_toy_tables(n_materials, n_nodes, _p(sig), _p(dedx), _p(le), _p(idl))
     if st != ET_OK:
         raise EtError(st, "et_build_toy_tables")
+    return {"sigma": sig, "dedx": dedx, "log_emin": float(le[0]), "inv_dlog": float(idl[0])}
+
+
+def et_build_toy_tables_fp64(n_materials=2, n_nodes=257):
+    sig = np.zeros((n_materials, 5, n_nodes), dtype=np.float64)
+    dedx = np.zeros(n_materials, dtype=np.float64)
+    le = np.zeros(1, np.float64)
+    idl = np.zeros(1, np.float64)
+    st = lib.et_build_toy_tables_fp64(n_materials, n_nodes, _p(sig), _p(dedx), _p(le), _p(idl))
+    if st != ET_OK:
+        raise EtError(st, "et_build_toy_tables_fp64")
     return {"sigma": sig, "dedx": dedx, "log_emin": float(le[0]), "inv_dlog": float(idl[0])}
 
 
@@ -381,6 +396,27 @@ def et_transport_noalloc(geom, tables, primaries_device, n_primaries, seed, n_ev
     if st != ET_OK:
         raise EtError(st, err.value.decode())
     return steps.value
+
+
+def et_run_fp64(geom, tables64, primaries: np.ndarray, seed, n_events, capacity_log2=22):
+    """The all-FP64 transport of one batch (see et.h).  tables64: et_build_toy_tables_fp64().
+    Returns (score[n_events][n_slabs], ledger[n_events][5], steps, iterations)."""
+    th = np.ascontiguousarray(geom["thickness"], dtype=np.float64)
+    mat = np.ascontiguousarray(geom["material"], dtype=np.uint8)
+    sig = np.ascontiguousarray(tables64["sigma"], dtype=np.float64)
+    dedx = np.ascontiguousarray(tables64["dedx"], dtype=np.float64)
+    p = np.ascontiguousarray(primaries)
+    assert p.dtype == PRIMARY_DTYPE
+    score = np.zeros((n_events, len(th)), np.float64)
+    ledger = np.zeros((n_events, 5), np.float64)
+    steps, iters = C.c_uint64(), C.c_uint64()
+    st = lib.et_run_fp64(len(th), _p(th), _p(mat), float(geom["half_xy"]), sig.shape[0],
+                         float(tables64["log_emin"]), float(tables64["inv_dlog"]), _p(sig),
+                         _p(dedx), _p(p), len(p), seed, n_events, capacity_log2, _p(score),
+                         _p(ledger), C.byref(steps), C.byref(iters))
+    if st != ET_OK:
+        raise EtError(st, "et_run_fp64")
+    return score, ledger, steps.value, iters.value
 
 
 def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) -> Context:

@@ -1,0 +1,105 @@
+"""Precision comparison on the mixed-primary workload (10,000 primaries: 50% e-, 25% e+,
+25% photons, log-uniform 100 MeV - 100 GeV, 1 cm^2 spot; one event each), GPU needed.
+
+Runs the same primaries through
+  fp32     the tuned path: FP32 state and stepping (strict mode), FP64 deposits and ledger
+  fp64     the all-FP64 GPU build
+  oracle64 the FP64 reference oracle (CPU, all cores)
+  oracle32 the strict FP32 oracle (CPU, all cores; the bit-exact target of fp32)
+and prints one JSON object with, per layer (absorber + gap summed), the mean deposit per
+primary and its standard error, each result's error against oracle64, and the run times.
+
+    python tests/precision_report.py [--n 10000] [--out FILE]
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+sys.path.insert(0, HERE)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--capacity-log2", type=int, default=24)
+    a = ap.parse_args()
+
+    import torch
+
+    import oracle
+    from paper_2302_08252_gb300 import et
+    from paper_2302_08252_gb300 import workloads as W
+    from parity import run_gpu
+
+    geom = W.calorimeter()
+    n = a.n
+    p = W.mixed_primaries(n)
+    e_in = p["ekin"].astype(np.float64)
+    res = {"workload": f"{n} mixed primaries (50% e-, 25% e+, 25% gamma), 0.1-100 GeV "
+                       "log-uniform, 1 cm^2 spot, one event each", "runs": {}}
+
+    t = time.perf_counter()
+    g = run_gpu(geom, p, n, form="dense", layout="aosoa32", driver="persistent", mode=0,
+                id_log=False, capacity_log2=a.capacity_log2)
+    torch.cuda.synchronize()
+    res["runs"]["fp32"] = {"seconds": time.perf_counter() - t, "steps": int(sum(g["counters"]["steps"]))}
+    t = time.perf_counter()
+    s64, l64, steps64, it64 = et.et_run_fp64(geom, et.et_build_toy_tables_fp64(), p, 1, n,
+                                             a.capacity_log2)
+    res["runs"]["fp64"] = {"seconds": time.perf_counter() - t, "steps": int(steps64)}
+    nth = os.cpu_count() or 1
+    t = time.perf_counter()
+    o64 = oracle.run(geom, p, n_events=n, seed=1, mode=oracle.REF_FP64, nthreads=nth)
+    res["runs"]["oracle64"] = {"seconds": time.perf_counter() - t,
+                               "steps": int(o64["steps"].sum()), "threads": nth}
+    t = time.perf_counter()
+    o32 = oracle.run(geom, p, n_events=n, seed=1, mode=oracle.STRICT_FP32, nthreads=nth)
+    res["runs"]["oracle32"] = {"seconds": time.perf_counter() - t,
+                               "steps": int(o32["steps"].sum()), "threads": nth}
+
+    def layers(score):
+        return score.reshape(n, -1, 2).sum(2)  # [event][layer]
+
+    ref = layers(o64["score"])
+    ref_mean = ref.mean(0)
+    big = ref_mean >= 0.01 * ref_mean.sum()
+    res["layer_mean_mev_oracle64"] = [float(x) for x in ref_mean]
+    res["layer_se_mev_oracle64"] = [float(x) for x in ref.std(0, ddof=1) / np.sqrt(n)]
+    for name, score in (("fp32", g["score"]), ("fp64", s64), ("oracle32", o32["score"])):
+        lg = layers(score)
+        diff = lg.mean(0) - ref_mean
+        se = np.sqrt(ref.var(0, ddof=1) / n + lg.var(0, ddof=1) / n)
+        ev = np.abs(score - o64["score"]) / e_in[:, None]
+        res[name] = {
+            "layer_rel_err_max_big_layers": float(np.max(np.abs(diff[big]) / ref_mean[big])),
+            "layer_err_in_se_max": float(np.max(np.abs(diff) / np.maximum(se, 1e-300))),
+            "total_deposit_rel_err": float(diff.sum() / ref_mean.sum()),
+            "per_event_slab_abs_err_over_e_max": float(ev.max()),
+            "steps_rel_diff": float(res["runs"][name]["steps"] / res["runs"]["oracle64"]["steps"] - 1.0),
+        }
+    # the bit-exact pair
+    res["fp32_vs_oracle32"] = {
+        "steps_equal": bool(g["counters"]["steps"] == [int(x) for x in o32["steps"]]),
+        "counts_equal": bool(np.array_equal(g["counts"].astype(np.int64),
+                                            o32["counts"].astype(np.int64))),
+        "deposit_rel_err_max": float(np.max(np.abs(g["score"] - o32["score"]) /
+                                            np.maximum(np.abs(o32["score"]), 1e-300))),
+    }
+    res["fp64_vs_oracle64"] = {"steps_equal": int(steps64) == int(o64["steps"].sum()),
+                               "iterations": [int(it64), int(o64["n_iters"])]}
+    line = json.dumps(res)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(line + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -48,6 +48,17 @@ def test_toy_tables_match_oracle_bit_for_bit(libet):
     assert mine["inv_dlog"] == ref["inv_dlog32"]
 
 
+def test_fp64_toy_tables_match_oracle(libet):
+    import oracle
+    from paper_2302_08252_gb300 import et
+    mine = et.et_build_toy_tables_fp64()
+    ref = oracle.build_tables()
+    assert np.allclose(mine["sigma"], ref["sig64"], rtol=1e-14, atol=0.0)
+    assert np.array_equal(mine["dedx"], ref["dedx64"])
+    assert mine["log_emin"] == ref["log_emin64"]
+    assert mine["inv_dlog"] == ref["inv_dlog64"]
+
+
 def test_create_without_gpu_fails_cleanly(libet):
     import torch
     if torch.cuda.is_available():
