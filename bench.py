@@ -207,7 +207,7 @@ def committed_traffic(kernel_key: str):
         with open(path) as f:
             d = json.load(f)
         from paper_2302_08252_gb300 import build
-        if d.get("fingerprint") != build._fingerprint():
+        if d.get("kernel_fingerprint") != build.kernel_fingerprint():
             return None
         return d.get("kernels", {}).get(kernel_key)
     except (OSError, ValueError):

@@ -44,7 +44,26 @@ def _fingerprint() -> str:
         with open(p, "rb") as f:
             h.update(p.encode())
             h.update(f.read())
-    h.update(" ".join(COMMON + STRICT + FAST).encode())
+    flags = [f for f in COMMON if f not in (INC, CSRC)] + STRICT + FAST  # no machine paths
+    h.update(" ".join(flags).encode())
+    return h.hexdigest()
+
+
+# The sources the transport kernels (kernels_tu.cu) are compiled from.
+KERNEL_SOURCES = ("kernels_tu.cu", "kernels.cuh", "physics.cuh", "layout.cuh", "common.cuh",
+                  "registry.h")
+
+
+def kernel_fingerprint() -> str:
+    """Hash of the transport kernels' sources and flags: a profile taken on one build
+    stays valid while this is unchanged (host-side code may change)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    flags = [f for f in COMMON if f not in (INC, CSRC)] + STRICT + FAST  # no machine paths
+    h.update(" ".join(flags).encode())
     return h.hexdigest()
 
 
