@@ -140,6 +140,10 @@ typedef struct {
 /*
  * Inject n primaries (host array, copied): they become active tracks of the
  * next iteration.  Their injected energy is added to their events' ledgers.
+ * The array is copied into the context's pinned staging before the call
+ * returns; the transfer to the device and the injection kernel then run
+ * asynchronously on the stream (a later et_inject waits for the staging to
+ * be free).
  */
 et_status et_inject(et_ctx* ctx, const et_primary* primaries, size_t n);
 
@@ -165,7 +169,10 @@ et_status et_run_iteration(et_ctx* ctx, et_iter_stats* out);
 /*
  * Iterate until no track is left or max_iters more iterations ran, with the
  * configured driver (host loop, CUDA graph, persistent kernel).  Totals and
- * the number of iterations run are optional outputs.
+ * the number of iterations run are optional outputs.  The persistent driver
+ * issues one launch and one read-back (the launch records its starting
+ * counters); the others read the counters back before they start.  Returns
+ * after the stream has finished the run.
  */
 et_status et_run_until_empty(et_ctx* ctx, uint64_t max_iters, et_iter_stats* totals,
                              uint64_t* n_iters);

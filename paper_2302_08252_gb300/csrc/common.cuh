@@ -88,6 +88,12 @@ struct alignas(16) DevCtl {
   // [free_head, free_snap) may be taken in this iteration, slots freed in this iteration
   // are appended at free_tail and become takeable at the next iteration boundary
   uint32_t free_head[4], free_tail[4], free_snap[4];  // word cw(t)
+  // persistent driver: a non-zero stop_rel stops the launch after that many iterations
+  // (instead of at stop_iter); the launch records where it started, so that the host
+  // needs no read-back before it
+  uint32_t stop_rel;
+  uint32_t run_iter0;
+  unsigned long long run_steps0[NTYPES], run_sec0[NTYPES];
 };
 
 // Iteration boundary bookkeeping of the slot-reuse rings (one thread, all other

@@ -43,11 +43,16 @@ struct et_ctx {
   DevCtl* d_ctl = nullptr;
   DevCtl* h_ctl = nullptr;  // pinned
   uint32_t* h_stop = nullptr;  // pinned scratch for stop_iter uploads
+  double* h_ledger = nullptr;  // pinned staging of the ledgers (allocated on first read)
   bool have_geom = false, have_tables = false;
   std::vector<float> planes;
   std::vector<uint8_t> mat;
   Primary* d_stage = nullptr;
   size_t stage_cap = 0;
+  Primary* h_stage = nullptr;  // pinned host staging of et_inject's primaries
+  size_t h_stage_cap = 0;
+  cudaEvent_t h_stage_done = nullptr;  // the last copy out of h_stage
+  bool h_stage_pending = false;
   int block = 256;
   int grid_fixed[3] = {0, 0, 0};  // step kernels in the graph driver (grid-stride)
   int grid_persistent = 0;
@@ -258,6 +263,9 @@ et_status et_destroy(et_ctx* c) {
   }
   if (c->h_ctl) cudaFreeHost(c->h_ctl);
   if (c->h_stop) cudaFreeHost(c->h_stop);
+  if (c->h_ledger) cudaFreeHost(c->h_ledger);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->h_stage_done) cudaEventDestroy(c->h_stage_done);
   (void)cudaGetLastError();
   delete c;
   return ET_OK;
@@ -278,8 +286,8 @@ et_status et_reset(et_ctx* c) {
     for (int h = 0; h < 2; ++h)
       if (a.heat[t][h])
         CUDA_TRY(c, cudaMemsetAsync(a.heat[t][h], 0, (size_t)c->cap * 64u, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  timing_collect(c);  // kernel timing accumulates across resets until et_read_timing
+  // no host synchronisation: the clears are ordered before later work on the stream, and
+  // kernel timings recorded so far are collected at the next read-back
   c->launches = 0;
   memset(c->h_ctl, 0, sizeof(DevCtl));
   return ET_OK;
@@ -411,7 +419,29 @@ et_status et_inject(et_ctx* c, const et_primary* p, size_t n) {
     if (!c->d_stage) return fail(c, ET_ERR_NOMEM, "primary staging");
     c->stage_cap = n;
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, p, n * sizeof(Primary), cudaMemcpyHostToDevice, c->stream));
+  // the caller's array is copied into pinned staging before returning (it may change or
+  // go away afterwards); the copy to the device then runs asynchronously on the stream
+  if (c->h_stage_pending) {
+    CUDA_TRY(c, cudaEventSynchronize(c->h_stage_done));  // the previous copy has read it
+    c->h_stage_pending = false;
+  }
+  if (n > c->h_stage_cap) {
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    c->h_stage = nullptr;
+    c->h_stage_cap = 0;
+    if (cudaMallocHost(&c->h_stage, n * sizeof(Primary)) != cudaSuccess) {
+      c->h_stage = nullptr;
+      return fail(c, ET_ERR_NOMEM, "pinned primary staging");
+    }
+    c->h_stage_cap = n;
+  }
+  if (!c->h_stage_done)
+    CUDA_TRY(c, cudaEventCreateWithFlags(&c->h_stage_done, cudaEventDisableTiming));
+  memcpy(c->h_stage, p, n * sizeof(Primary));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, c->h_stage, n * sizeof(Primary), cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->h_stage_done, c->stream));
+  c->h_stage_pending = true;
   uint32_t nn = (uint32_t)n;
   const Primary* dp = c->d_stage;
   void* params[] = {(void*)&c->args, (void*)&dp, (void*)&nn};
@@ -546,6 +576,31 @@ et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* total
                              uint64_t* n_iters) {
   if (!c) return ET_ERR_INVALID;
   if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (c->cfg.driver == ET_DRIVER_PERSISTENT && max_iters > 0) {
+    // one launch, one read-back: the kernel stops after max_iters iterations (or when no
+    // track is left) and records its starting iteration and counters for the totals
+    c->h_stop[1] = max_iters > 0xffffffffull ? 0xffffffffu : (uint32_t)max_iters;
+    CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_rel, c->h_stop + 1, 4, cudaMemcpyHostToDevice, c->stream));
+    int fault = c->fault_skip_block;
+    void* params[] = {(void*)&c->args, (void*)&fault};
+    const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+    EventPair* ev = timing_begin(c);
+    CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block), params,
+                                            c->smem_all, c->stream));
+    timing_end(c, ev);
+    c->launches += 1;
+    et_status s = sync_ctl(c);
+    if (s != ET_OK) return s;
+    DevCtl before = *c->h_ctl;
+    before.iter = c->h_ctl->run_iter0;
+    for (int t = 0; t < NTYPES; ++t) {
+      before.steps[t] = c->h_ctl->run_steps0[t];
+      before.secondaries[t] = c->h_ctl->run_sec0[t];
+    }
+    fill_stats(c, before, totals);
+    if (n_iters) *n_iters = c->h_ctl->iter - before.iter;
+    return ET_OK;
+  }
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   const DevCtl before = *c->h_ctl;
@@ -633,11 +688,15 @@ et_status et_read_scoring_all(et_ctx* c, double* score, et_ledger* ledger) {
     sc.resize(ne * ns);
     dst = sc.data();
   }
-  std::vector<double> lg(ledger ? ne * 5 : 0);
+  if (ledger && !c->h_ledger && cudaMallocHost(&c->h_ledger, ne * 5 * 8) != cudaSuccess) {
+    c->h_ledger = nullptr;
+    return fail(c, ET_ERR_NOMEM, "pinned ledger staging");
+  }
+  const double* lg = c->h_ledger;
   if (dst)
     CUDA_TRY(c, cudaMemcpyAsync(dst, c->args.score, ne * ns * 8, cudaMemcpyDeviceToHost, c->stream));
   if (ledger)
-    CUDA_TRY(c, cudaMemcpyAsync(lg.data(), c->args.ledger, ne * 5 * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_ledger, c->args.ledger, ne * 5 * 8, cudaMemcpyDeviceToHost, c->stream));
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   if (ledger) {

@@ -579,36 +579,42 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Returns false if this block gave up waiting (status ST_TIMEOUT is then set).
+// Returns false if this block gave up waiting (status ST_TIMEOUT is then set).  `gen` is
+// thread 0's copy of the barrier generation (read once at kernel start: it cannot move
+// before every block has arrived at the first barrier); `rings`: the sparse form's slot
+// reuse rings move their boundary here.
 static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long timeout_ns,
-                          uint32_t* snap_status) {
+                                 uint32_t* snap_status, uint32_t& gen, bool rings) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> gen(c->bar_gen);
+    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> g_ref(c->bar_gen);
     cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(c->bar_count);
     cuda::atomic_ref<uint32_t, cuda::thread_scope_device> st(c->status);
-    const uint32_t g = gen.load(cuda::memory_order_acquire);
-    __threadfence();
-    const uint32_t arrived = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+    const uint32_t g = gen;
+    __threadfence();  // this block's writes before the arrival
+    const uint32_t arrived = cnt.fetch_add(1u, cuda::memory_order_relaxed);
     int ok = 1;
     if (arrived == nblocks - 1) {
+      __threadfence();  // the other blocks' writes (status bits, rings) before the reads below
       cnt.store(0u, cuda::memory_order_relaxed);
       *snap_status = st.load(cuda::memory_order_relaxed);
-      free_ring_boundary(c);  // every other block is waiting here: no slot is being taken
-      gen.store(g + 1u, cuda::memory_order_release);
+      if (rings) free_ring_boundary(c);  // every other block is waiting: no slot is being taken
+      __threadfence();
+      g_ref.store(g + 1u, cuda::memory_order_relaxed);
     } else {
       const unsigned long long t0 = global_ns();
-      while (gen.load(cuda::memory_order_acquire) == g) {
+      while (g_ref.load(cuda::memory_order_relaxed) == g) {
         if (global_ns() - t0 > timeout_ns) {
           st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
           ok = 0;
           break;
         }
-        __nanosleep(40);
+        __nanosleep(32);
       }
     }
-    __threadfence();
+    __threadfence();  // the other blocks' writes before this block's next reads
+    gen = g + 1u;
     ok_s = ok;
   }
   __syncthreads();
@@ -641,8 +647,18 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   if ((int)blockIdx.x == fault_skip_block) return;  // host-side fault injection: never arrives
   uint32_t it = *(volatile uint32_t*)&c->iter;
-  const uint32_t stop_iter = *(volatile uint32_t*)&c->stop_iter;
+  const uint32_t stop_rel = *(volatile uint32_t*)&c->stop_rel;
+  const uint32_t stop_iter = stop_rel == 0u ? *(volatile uint32_t*)&c->stop_iter
+                             : (it + stop_rel < it ? 0xffffffffu : it + stop_rel);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // before this block's first barrier: no other
+    c->run_iter0 = it;                        // block can have changed these yet
+    for (int t = 0; t < NTYPES; ++t) {
+      c->run_steps0[t] = c->steps[t];
+      c->run_sec0[t] = c->secondaries[t];
+    }
+  }
   uint32_t status0 = *(volatile uint32_t*)&c->status;
+  uint32_t bar_gen = threadIdx.x == 0 ? *(volatile uint32_t*)&c->bar_gen : 0u;
   bool first = true;
   Tally tl;  // flushed when the loop ends
   tally_reset(tl);
@@ -694,7 +710,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       }
       process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, batch, drain_all, tl);
     }
-    if (!grid_sync(c, gridDim.x, a.timeout_ns, snap)) return;
+    if (!grid_sync(c, gridDim.x, a.timeout_ns, snap, bar_gen, a.free_ring[0] != nullptr)) return;
     if (DENSE && blockIdx.x == 0 && threadIdx.x == 0) {
       for (int t = 0; t < 3; ++t) {
         const uint32_t fill = __ldcg(&c->cnt[(it + 1) % 3][cw(t)]);

@@ -277,9 +277,18 @@ def et_read_scoring(ctx, event, n_slabs):
     return dep, {f: getattr(lg, f) for f, _ in et_ledger._fields_}
 
 
-def et_read_scoring_all(ctx, max_events, n_slabs):
-    score = np.zeros((max_events, n_slabs), dtype=np.float64)
-    ledger = np.zeros((max_events, 6), dtype=np.float64)
+def et_read_scoring_all(ctx, max_events, n_slabs, out=None):
+    """Per-slab deposits [max_events][n_slabs] and ledgers [max_events][6].  `out`: an
+    optional (score, ledger) pair of float64 arrays to fill (e.g. views of pinned memory,
+    which the device copies into directly)."""
+    if out is None:
+        score = np.zeros((max_events, n_slabs), dtype=np.float64)
+        ledger = np.zeros((max_events, 6), dtype=np.float64)
+    else:
+        score, ledger = out
+        assert score.dtype == np.float64 and score.shape == (max_events, n_slabs)
+        assert ledger.dtype == np.float64 and ledger.shape == (max_events, 6)
+        assert score.flags.c_contiguous and ledger.flags.c_contiguous
     _check(ctx, lib.et_read_scoring_all(ctx.handle, _p(score), _p(ledger)))
     return score, ledger
 
