@@ -52,7 +52,17 @@ typedef enum {
 
 enum { ET_EMINUS = 0, ET_EPLUS = 1, ET_GAMMA = 2, ET_NTYPES = 3 };
 enum { ET_FORM_SPARSE = 0, ET_FORM_DENSE = 1 };
-enum { ET_LAYOUT_AOS = 0, ET_LAYOUT_SOA = 1, ET_LAYOUT_AOSOA32 = 2, ET_LAYOUT_AOSOA64 = 3 };
+/* AoSoA-N: blocks of N records, each leaf stored N-wide inside its block (Sec. 3-4);
+ * AoSoA-128 needs capacity_log2 >= 7. */
+enum {
+  ET_LAYOUT_AOS = 0,
+  ET_LAYOUT_SOA = 1,
+  ET_LAYOUT_AOSOA32 = 2,
+  ET_LAYOUT_AOSOA64 = 3,
+  ET_LAYOUT_AOSOA8 = 4,
+  ET_LAYOUT_AOSOA16 = 5,
+  ET_LAYOUT_AOSOA128 = 6
+};
 enum { ET_MODE_STRICT = 0, ET_MODE_FAST = 1 };
 enum { ET_DRIVER_HOSTLOOP = 0, ET_DRIVER_GRAPH = 1, ET_DRIVER_PERSISTENT = 2 };
 

@@ -22,7 +22,7 @@ import time
 
 import numpy as np
 
-LAYOUTS = ("aos", "soa", "aosoa32", "aosoa64")
+LAYOUTS = ("aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128")
 BLOCKS = (64, 128, 256)
 DRIVERS = ("persistent", "graph", "hostloop")
 

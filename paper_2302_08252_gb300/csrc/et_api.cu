@@ -102,11 +102,13 @@ static void* dalloc(et_ctx* c, size_t bytes) {
 }
 
 static void register_kernels(int mode, int layout, KernelSet* ks) {
-  static void (*const fns[2][4])(KernelSet*) = {
+  static void (*const fns[2][N_LAYOUTS])(KernelSet*) = {
       {et_register_kernels_0_0, et_register_kernels_0_1, et_register_kernels_0_2,
-       et_register_kernels_0_3},
+       et_register_kernels_0_3, et_register_kernels_0_4, et_register_kernels_0_5,
+       et_register_kernels_0_6},
       {et_register_kernels_1_0, et_register_kernels_1_1, et_register_kernels_1_2,
-       et_register_kernels_1_3}};
+       et_register_kernels_1_3, et_register_kernels_1_4, et_register_kernels_1_5,
+       et_register_kernels_1_6}};
   fns[mode][layout](ks);
 }
 
@@ -170,7 +172,8 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   if (k.block_size == 0) k.block_size = 256;
   if (k.max_iters == 0) k.max_iters = 1u << 16;
   if (k.capacity_log2 < 6 || k.capacity_log2 > 28 || (k.form != 0 && k.form != 1) ||
-      k.layout < 0 || k.layout > 3 || (k.mode != 0 && k.mode != 1) || k.driver < 0 ||
+      k.layout < 0 || k.layout >= N_LAYOUTS || (k.mode != 0 && k.mode != 1) || k.driver < 0 ||
+      (k.layout == LAYOUT_AOSOA128 && k.capacity_log2 < 7) ||
       k.driver > 2 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
       k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) ||
       ((k.alloc == nullptr) != (k.free == nullptr)))

@@ -19,7 +19,16 @@
 
 namespace et {
 
-enum { LAYOUT_AOS = 0, LAYOUT_SOA = 1, LAYOUT_AOSOA32 = 2, LAYOUT_AOSOA64 = 3 };
+enum {
+  LAYOUT_AOS = 0,
+  LAYOUT_SOA = 1,
+  LAYOUT_AOSOA32 = 2,
+  LAYOUT_AOSOA64 = 3,
+  LAYOUT_AOSOA8 = 4,
+  LAYOUT_AOSOA16 = 5,
+  LAYOUT_AOSOA128 = 6,
+  N_LAYOUTS = 7
+};
 
 template <int L>
 struct Layout;
@@ -49,6 +58,12 @@ template <>
 struct Layout<LAYOUT_AOSOA32> : AoSoA<32> {};
 template <>
 struct Layout<LAYOUT_AOSOA64> : AoSoA<64> {};
+template <>
+struct Layout<LAYOUT_AOSOA8> : AoSoA<8> {};
+template <>
+struct Layout<LAYOUT_AOSOA16> : AoSoA<16> {};
+template <>
+struct Layout<LAYOUT_AOSOA128> : AoSoA<128> {};
 
 // Instrumentation sink: trace[type][leaf][0 read / 1 write] and a per-word heatmap.
 struct Instr {

@@ -17,8 +17,14 @@ void et_register_kernels_0_0(et::KernelSet*);
 void et_register_kernels_0_1(et::KernelSet*);
 void et_register_kernels_0_2(et::KernelSet*);
 void et_register_kernels_0_3(et::KernelSet*);
+void et_register_kernels_0_4(et::KernelSet*);
+void et_register_kernels_0_5(et::KernelSet*);
+void et_register_kernels_0_6(et::KernelSet*);
 void et_register_kernels_1_0(et::KernelSet*);
 void et_register_kernels_1_1(et::KernelSet*);
 void et_register_kernels_1_2(et::KernelSet*);
 void et_register_kernels_1_3(et::KernelSet*);
+void et_register_kernels_1_4(et::KernelSet*);
+void et_register_kernels_1_5(et::KernelSet*);
+void et_register_kernels_1_6(et::KernelSet*);
 }

@@ -23,8 +23,10 @@ LIB_PATH = os.path.join(HERE, "_build", "libet.so")
 ET_OK, ET_ERR_INVALID, ET_ERR_CAPACITY, ET_ERR_CUDA, ET_ERR_TIMEOUT, ET_ERR_STATE, ET_ERR_NOMEM = \
     range(7)
 FORM_SPARSE, FORM_DENSE = 0, 1
-LAYOUT_AOS, LAYOUT_SOA, LAYOUT_AOSOA32, LAYOUT_AOSOA64 = range(4)
-LAYOUTS = {"aos": 0, "soa": 1, "aosoa32": 2, "aosoa64": 3}
+LAYOUT_AOS, LAYOUT_SOA, LAYOUT_AOSOA32, LAYOUT_AOSOA64, LAYOUT_AOSOA8, LAYOUT_AOSOA16, \
+    LAYOUT_AOSOA128 = range(7)
+LAYOUTS = {"aos": 0, "soa": 1, "aosoa32": 2, "aosoa64": 3, "aosoa8": 4, "aosoa16": 5,
+           "aosoa128": 6}
 MODE_STRICT, MODE_FAST = 0, 1
 DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT = range(3)
 DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2}

@@ -82,7 +82,8 @@ def trace_table(trace: np.ndarray, names=("e-", "e+", "gamma")) -> str:
 def leaf_address(layout: str, i: int, f: int, cap: int) -> int:
     """Byte address of leaf f of track i (same mapping as the device layout layer)."""
     _, off, size = LEAVES[f]
-    n = {"aos": 1, "soa": cap, "aosoa32": 32, "aosoa64": 64}[layout]
+    n = {"aos": 1, "soa": cap, "aosoa8": 8, "aosoa16": 16, "aosoa32": 32, "aosoa64": 64,
+         "aosoa128": 128}[layout]
     return (i // n) * 64 * n + off * n + size * (i % n)
 
 

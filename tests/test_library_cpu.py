@@ -88,3 +88,17 @@ def test_invalid_config_rejected(libet):
     h = ctypes.c_void_p()
     assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
     assert not h.value
+
+
+def test_aosoa128_needs_a_full_block(libet):
+    from paper_2302_08252_gb300 import et
+    cfg = et.et_config()
+    cfg.capacity_log2 = 6     # 64 slots: less than one AoSoA-128 block
+    cfg.layout = et.LAYOUT_AOSOA128
+    cfg.max_events = 1
+    cfg.block_size = 256
+    h = ctypes.c_void_p()
+    assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
+    cfg.layout = 7            # no such layout
+    cfg.capacity_log2 = 10
+    assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
