@@ -61,7 +61,8 @@ enum {
   ET_LAYOUT_AOSOA64 = 3,
   ET_LAYOUT_AOSOA8 = 4,
   ET_LAYOUT_AOSOA16 = 5,
-  ET_LAYOUT_AOSOA128 = 6
+  ET_LAYOUT_AOSOA128 = 6,
+  ET_LAYOUT_HOTCOLD = 7  /* hot 52 bytes AoSoA-32, cold time/length/flags SoA */
 };
 enum { ET_MODE_STRICT = 0, ET_MODE_FAST = 1 };
 enum { ET_DRIVER_HOSTLOOP = 0, ET_DRIVER_GRAPH = 1, ET_DRIVER_PERSISTENT = 2 };
@@ -88,7 +89,9 @@ typedef struct {
   et_free_fn free;
   void* alloc_user;
   int32_t serving;          /* 1: count live tracks per event and report completed events
-                               (et_poll_completed), for continuous batching */
+                               (et_poll_completed), for continuous batching; the iteration
+                               count log then wraps (iteration it at entry it % max_iters)
+                               instead of filling up */
   int32_t reuse_slots;      /* sparse form: 1 = slots of dead tracks are reused (from the next
                                iteration on); 0 = never reused (the plain single buffer) */
 } et_config;

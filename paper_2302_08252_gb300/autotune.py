@@ -22,7 +22,7 @@ import time
 
 import numpy as np
 
-LAYOUTS = ("aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128")
+LAYOUTS = ("aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128", "hotcold")
 BLOCKS = (64, 128, 256)
 DRIVERS = ("persistent", "graph", "hostloop")
 
@@ -89,3 +89,50 @@ def cached(path: str, key: str, compute):
         with open(path, "w") as f:
             json.dump(data, f, indent=1)
     return data[key]
+
+
+def main(argv=None):
+    """Tune on a sample of a workload's events, then time the chosen configuration and each
+    driver at the default layout on the whole workload (GPU).
+
+        python -m paper_2302_08252_gb300.autotune [--workload uneven] [--sample 32]
+            [--capacity-log2 26] [--out FILE]
+    """
+    import argparse
+
+    from . import study
+    from . import workloads as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="uneven", choices=["jittered", "small", "mixed", "uneven"])
+    ap.add_argument("--sample", type=int, default=32)
+    ap.add_argument("--capacity-log2", type=int, default=26)
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args(argv)
+    geom = W.calorimeter()
+    prim, n_events = study.workload(a.workload)
+    tuned = autotune(geom, prim, n_events, sample=a.sample, reps=a.reps,
+                     capacity_log2=min(a.capacity_log2, 24))  # a sample needs fewer slots
+    b = tuned["best"]
+    steps = study.steps_of(geom, prim, n_events, "dense", b["layout"], b["driver"],
+                           a.capacity_log2)
+    full = []
+    for layout, block, driver in [(b["layout"], b["block_size"], b["driver"]),
+                                  ("aosoa32", 256, "persistent"), ("aosoa32", 256, "graph"),
+                                  ("aosoa32", 256, "hostloop")]:
+        t = time_config(geom, prim, n_events, "dense", layout, block, driver, a.reps,
+                        a.capacity_log2)
+        full.append({"layout": layout, "block_size": block, "driver": driver, "seconds": t,
+                     "track_steps_per_s": steps / t})
+        print(json.dumps(full[-1]), flush=True)
+    res = {"workload": a.workload, "events": n_events, "primaries": int(len(prim)),
+           "steps": steps, "tuned_on_events": tuned["tuned_on_events"], "best": b,
+           "table": tuned["table"], "full": full}
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(res, f, indent=1)
+    return res
+
+
+if __name__ == "__main__":
+    main()

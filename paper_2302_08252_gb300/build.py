@@ -70,7 +70,7 @@ def kernel_fingerprint() -> str:
 def _jobs():
     jobs = []
     for mode in (0, 1):
-        for layout in range(7):
+        for layout in range(8):
             obj = os.path.join(OUT, f"k_{mode}_{layout}.o")
             flags = STRICT if mode == 0 else FAST
             jobs.append([_nvcc(), *COMMON, *flags, f"-DET_MODE={mode}", f"-DET_LAYOUT={layout}",

@@ -92,6 +92,7 @@ struct alignas(16) DevCtl {
   // (instead of at stop_iter); the launch records where it started, so that the host
   // needs no read-back before it
   uint32_t stop_rel;
+  uint32_t grab[4];  // persistent driver: dynamic chunk counter of iteration it (row it % 3)
   uint32_t run_iter0;
   unsigned long long run_steps0[NTYPES], run_sec0[NTYPES];
 };
@@ -121,6 +122,7 @@ struct Args {
   DevCtl* ctl;
   uint32_t* counts_log;         // [max_iters][3]
   uint32_t max_iters;
+  uint32_t iter_log_wrap;        // serving: the count log is a ring (entry it % max_iters)
   uint32_t n_slabs;
   double* score;                // [max_events][n_slabs]
   double* ledger;               // [max_events][5]: injected, cut, escaped, mass_created, mass_consumed

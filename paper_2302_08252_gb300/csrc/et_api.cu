@@ -105,10 +105,10 @@ static void register_kernels(int mode, int layout, KernelSet* ks) {
   static void (*const fns[2][N_LAYOUTS])(KernelSet*) = {
       {et_register_kernels_0_0, et_register_kernels_0_1, et_register_kernels_0_2,
        et_register_kernels_0_3, et_register_kernels_0_4, et_register_kernels_0_5,
-       et_register_kernels_0_6},
+       et_register_kernels_0_6, et_register_kernels_0_7},
       {et_register_kernels_1_0, et_register_kernels_1_1, et_register_kernels_1_2,
        et_register_kernels_1_3, et_register_kernels_1_4, et_register_kernels_1_5,
-       et_register_kernels_1_6}};
+       et_register_kernels_1_6, et_register_kernels_1_7}};
   fns[mode][layout](ks);
 }
 
@@ -216,6 +216,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   a.ctl = c->d_ctl = (DevCtl*)dalloc(c, sizeof(DevCtl));
   a.counts_log = (uint32_t*)dalloc(c, (size_t)k.max_iters * 3u * 4u);
   a.max_iters = k.max_iters;
+  a.iter_log_wrap = k.serving ? 1u : 0u;
   a.max_events = k.max_events;
   a.ledger = (double*)dalloc(c, (size_t)k.max_events * 5u * 8u);
   if (!a.ctl || !a.counts_log || !a.ledger) return fail(c, ET_ERR_NOMEM, "control block");
@@ -495,7 +496,7 @@ static et_status one_hostloop_iteration(et_ctx* c, bool* empty) {
   const uint32_t n[3] = {row[cw(EM)], row[cw(EP)], row[cw(GAM)]};
   *empty = (n[0] + n[1] + n[2]) == 0;
   if (*empty) return ET_OK;
-  if (it >= c->cfg.max_iters) return fail(c, ET_ERR_CAPACITY, "iteration log full");
+  if (it >= c->cfg.max_iters && !c->cfg.serving) return fail(c, ET_ERR_CAPACITY, "iteration log full");
   c->h_stop[0] = 0xffffffffu;
   CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
   s = launch_step_kernels(c, n, false);
@@ -559,13 +560,39 @@ static et_status build_graph(et_ctx* c) {
       cudaSuccess) {
     s = fail(c, ET_ERR_CUDA, "graph capture failed to start");
   } else {
-    const uint32_t n[3] = {1, 1, 1};
-    s = launch_step_kernels(c, n, true);
+    // the three per-type step kernels as parallel branches (fork/join through events), so
+    // that one type's sparse tail overlaps with the others' work; then the end node
+    cudaStream_t br[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool ok = true;
+    for (int k = 0; k < 2; ++k) ok = ok && cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 3; ++k) ok = ok && cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) s = fail(c, ET_ERR_CUDA, "graph branches");
+    if (s == ET_OK && (cudaEventRecord(ev[0], cs) != cudaSuccess ||
+                       cudaStreamWaitEvent(br[0], ev[0], 0) != cudaSuccess ||
+                       cudaStreamWaitEvent(br[1], ev[0], 0) != cudaSuccess))
+      s = fail(c, ET_ERR_CUDA, "graph fork");
+    const int instr = c->cfg.instrument ? 1 : 0, dn = c->dense ? 1 : 0;
+    void* params[] = {(void*)&c->args};
+    for (int t = 0; t < 3 && s == ET_OK; ++t) {
+      c->stream = t == 0 ? cs : br[t - 1];
+      s = launch(c, c->ks.step[instr][dn][t], c->grid_fixed[t], c->block, c->smem_all, params);
+    }
+    c->stream = cs;
+    if (s == ET_OK && (cudaEventRecord(ev[1], br[0]) != cudaSuccess ||
+                       cudaEventRecord(ev[2], br[1]) != cudaSuccess ||
+                       cudaStreamWaitEvent(cs, ev[1], 0) != cudaSuccess ||
+                       cudaStreamWaitEvent(cs, ev[2], 0) != cudaSuccess))
+      s = fail(c, ET_ERR_CUDA, "graph join");
     if (s == ET_OK) s = launch_end(c, h, 1);
     cudaGraph_t out_g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &out_g);
     if (s == ET_OK && e != cudaSuccess)
       s = fail(c, ET_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    for (int k = 0; k < 2; ++k)
+      if (br[k]) cudaStreamDestroy(br[k]);
+    for (int k = 0; k < 3; ++k)
+      if (ev[k]) cudaEventDestroy(ev[k]);
   }
   c->stream = saved;
   c->launches = saved_launches;

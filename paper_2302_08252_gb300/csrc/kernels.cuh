@@ -181,17 +181,22 @@ __device__ __forceinline__ Trk make_secondary(const Trk& parent, const Sec& s, i
   return r;
 }
 
+// Fire-and-forget FP64 add to global memory (no value comes back, so nothing waits on it).
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const StepOut& o) {
   const size_t ev = t.event;
-  if (o.dep_nz) atomicAdd(&a.score[ev * a.n_slabs + (size_t)o.slab_cont], o.dep);
+  if (o.dep_nz) red_add(&a.score[ev * a.n_slabs + (size_t)o.slab_cont], o.dep);
   if (o.bal) {
     if ((o.bal & B_CUT) && o.cut != 0.0) {
-      atomicAdd(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
-      atomicAdd(&a.ledger[ev * 5 + 1], o.cut);
+      red_add(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
+      red_add(&a.ledger[ev * 5 + 1], o.cut);
     }
-    if ((o.bal & B_ESC) && o.esc != 0.0f) atomicAdd(&a.ledger[ev * 5 + 2], f2d(o.esc));
-    if (o.bal & B_MCR) atomicAdd(&a.ledger[ev * 5 + 3], (double)MC2 + (double)MC2);
-    if ((o.bal & B_MC) && o.mc != 0.0) atomicAdd(&a.ledger[ev * 5 + 4], o.mc);
+    if ((o.bal & B_ESC) && o.esc != 0.0f) red_add(&a.ledger[ev * 5 + 2], f2d(o.esc));
+    if (o.bal & B_MCR) red_add(&a.ledger[ev * 5 + 3], (double)MC2 + (double)MC2);
+    if ((o.bal & B_MC) && o.mc != 0.0) red_add(&a.ledger[ev * 5 + 4], o.mc);
   }
 }
 
@@ -557,11 +562,12 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
   const uint32_t cur = it % 3, nxt = (it + 1) % 3;
   for (int t = 0; t < NTYPES; ++t) {
     c->steps[t] += c->cnt[cur][cw(t)];
-    if (it < a.max_iters) a.counts_log[(size_t)it * 3 + t] = c->cnt[cur][cw(t)];
+    const uint32_t li = a.iter_log_wrap ? it % a.max_iters : it;
+    if (li < a.max_iters) a.counts_log[(size_t)li * 3 + t] = c->cnt[cur][cw(t)];
     const uint32_t fill = c->cnt[nxt][cw(t)];
     if (a.idx[0][0] == nullptr && fill > c->hwm[cw(t)]) c->hwm[cw(t)] = fill;  // dense: peak fill
   }
-  if (it >= a.max_iters) c->status |= ST_ITER_LOG_FULL;
+  if (it >= a.max_iters && !a.iter_log_wrap) c->status |= ST_ITER_LOG_FULL;
   free_ring_boundary(c);
   for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
   c->iter = it + 1;
@@ -623,8 +629,9 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
 
 // ---- persistent kernel: all types, all iterations, one cooperative launch ----
 // Warp chunks of 32 tracks are type-uniform: the iteration's index space is
-// [ceil(n_e-/32) chunks of e-][chunks of e+][chunks of gamma], and warp w takes chunks
-// w, w + nw, ... (static order: a per-chunk atomic counter measured slower).
+// [ceil(n_e-/32) chunks of e-][chunks of e+][chunks of gamma].  Warp w takes chunks
+// w, w + nw, ... and, when the iteration gives every warp two or more chunks, the last
+// round from a per-iteration counter (a counter for every chunk measured slower).
 template <int MODE, int L, bool INSTR, bool DENSE>
 // Three resident blocks of 256 threads per SM (<= 80 registers per thread; a handful of
 // bytes spill): 24 warps per SM hide more of the step's dependent latency than 16 warps
@@ -678,15 +685,21 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       for (int t = 0; t < 3; ++t) {
         c->cnt[(it + 2) % 3][t] = 0;
         c->steps[t] += s_n[t];
-        if (it < a.max_iters) a.counts_log[(size_t)it * 3 + t] = s_n[t];
+        const uint32_t li = a.iter_log_wrap ? it % a.max_iters : it;
+        if (li < a.max_iters) a.counts_log[(size_t)li * 3 + t] = s_n[t];
       }
-      if (it >= a.max_iters) atomicOr(&c->status, ST_ITER_LOG_FULL);
+      if (it >= a.max_iters && !a.iter_log_wrap) atomicOr(&c->status, ST_ITER_LOG_FULL);
     }
     const uint32_t w0 = (n0 + 31) / 32, w1 = (n1 + 31) / 32, w2 = (n2 + 31) / 32;
     const uint32_t wt = w0 + w1 + w2;
-    // static chunk order: warp w takes chunks w, w + nw, ...; the type changes at most
-    // twice per warp and iteration, and the queue is emptied at each change
+    // chunk order: warp w takes chunks w, w + nw, ... below S, then the rest from a counter
+    // (the last round of each iteration goes to the warps that finish first); a warp's
+    // chunk indices increase, so its type changes at most twice per iteration, and the
+    // queue is emptied at each change
     const bool batch = wt >= 2u * nw;  // each warp sees several chunks: batching pays
+    const uint32_t S = batch ? (wt / nw - 1u) * nw : wt;
+    uint32_t* grab = &c->grab[it % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->grab[(it + 2) % 3] = 0u;  // last used in it - 1
     uint32_t ch = batch ? gw_major : gw_spread;
     int qtype = EM;
     while (ch < wt || wq.count) {
@@ -701,7 +714,12 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
           const uint32_t nt = ty == EM ? n0 : (ty == EP ? n1 : n2);
           i = (ch - base) * 32u + lane;
           valid = i < nt;
-          const uint32_t nxt = ch + nw;
+          uint32_t nxt = ch + nw;
+          if (batch && nxt >= S) {
+            uint32_t g = 0;
+            if (lane == 0) g = atomicAdd(grab, 1u);
+            nxt = S + __shfl_sync(FULL, g, 0);
+          }
           const int nty = nxt < wt ? (nxt < w0 ? EM : (nxt < w0 + w1 ? EP : GAM)) : -1;
           drain_all = nty != ty;  // the warp's last chunk of this type
           ch = nxt;
@@ -724,6 +742,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
     c->iter = it;
     const uint32_t cur = it % 3;
     for (int t = 0; t < 3; ++t) c->cnt[(it + 2) % 3][t] = 0;  // between iterations only cur is non-zero
+    for (int t = 0; t < 3; ++t) c->grab[t] = 0u;
     c->done =(__ldcg(&c->cnt[cur][0]) + __ldcg(&c->cnt[cur][1]) + __ldcg(&c->cnt[cur][2]) == 0);
   }
 }

@@ -9,6 +9,7 @@
 //   AoS        base + 64 i + off_f
 //   SoA        base + off_f cap + s_f i
 //   AoSoA-N    base + 64 N (i / N) + off_f N + s_f (i mod N)
+//   hot/cold   see Layout<LAYOUT_HOTCOLD>
 // (AoSoA-N with N = 1 is AoS and with N = cap is SoA).  All leaves are 4 or
 // 8 bytes and naturally aligned, so each access touches whole 4-byte words;
 // the heatmap counts per 4-byte word, which equals the per-byte count of each
@@ -27,7 +28,8 @@ enum {
   LAYOUT_AOSOA8 = 4,
   LAYOUT_AOSOA16 = 5,
   LAYOUT_AOSOA128 = 6,
-  N_LAYOUTS = 7
+  LAYOUT_HOTCOLD = 7,
+  N_LAYOUTS = 8
 };
 
 template <int L>
@@ -64,6 +66,24 @@ template <>
 struct Layout<LAYOUT_AOSOA16> : AoSoA<16> {};
 template <>
 struct Layout<LAYOUT_AOSOA128> : AoSoA<128> {};
+// Hot/cold split: the 52 bytes the step's decisions read (position, direction, energy,
+// interaction lengths, id, event, step count, slab) as AoSoA-32, and the three fields
+// that are only accumulated (time, track length, flags: byte offsets 52-63) as SoA
+// arrays after them:
+//   hot  leaf f   base + 52*32 (i / 32) + off_f 32 + s_f (i mod 32)
+//   cold leaf f   base + 52 cap + (off_f - 52) cap + 4 i
+// The buffer is still cap * 64 bytes; cap is a multiple of 32.
+template <>
+struct Layout<LAYOUT_HOTCOLD> {
+  static constexpr int lanes = 32;
+  static constexpr int kHot = 52;
+  __device__ static size_t addr(uint32_t i, int f, uint32_t cap) {
+    const int off = leaf_off(f);
+    if (off < kHot)
+      return (size_t)(i / 32u) * (kHot * 32u) + (size_t)off * 32u + (size_t)leaf_size(f) * (i % 32u);
+    return (size_t)kHot * cap + (size_t)(off - kHot) * cap + 4u * (size_t)i;
+  }
+};
 
 // Instrumentation sink: trace[type][leaf][0 read / 1 write] and a per-word heatmap.
 struct Instr {

@@ -20,6 +20,7 @@ void et_register_kernels_0_3(et::KernelSet*);
 void et_register_kernels_0_4(et::KernelSet*);
 void et_register_kernels_0_5(et::KernelSet*);
 void et_register_kernels_0_6(et::KernelSet*);
+void et_register_kernels_0_7(et::KernelSet*);
 void et_register_kernels_1_0(et::KernelSet*);
 void et_register_kernels_1_1(et::KernelSet*);
 void et_register_kernels_1_2(et::KernelSet*);
@@ -27,4 +28,5 @@ void et_register_kernels_1_3(et::KernelSet*);
 void et_register_kernels_1_4(et::KernelSet*);
 void et_register_kernels_1_5(et::KernelSet*);
 void et_register_kernels_1_6(et::KernelSet*);
+void et_register_kernels_1_7(et::KernelSet*);
 }

@@ -24,9 +24,9 @@ ET_OK, ET_ERR_INVALID, ET_ERR_CAPACITY, ET_ERR_CUDA, ET_ERR_TIMEOUT, ET_ERR_STAT
     range(7)
 FORM_SPARSE, FORM_DENSE = 0, 1
 LAYOUT_AOS, LAYOUT_SOA, LAYOUT_AOSOA32, LAYOUT_AOSOA64, LAYOUT_AOSOA8, LAYOUT_AOSOA16, \
-    LAYOUT_AOSOA128 = range(7)
+    LAYOUT_AOSOA128, LAYOUT_HOTCOLD = range(8)
 LAYOUTS = {"aos": 0, "soa": 1, "aosoa32": 2, "aosoa64": 3, "aosoa8": 4, "aosoa16": 5,
-           "aosoa128": 6}
+           "aosoa128": 6, "hotcold": 7}
 MODE_STRICT, MODE_FAST = 0, 1
 DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT = range(3)
 DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2}

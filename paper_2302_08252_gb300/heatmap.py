@@ -82,6 +82,10 @@ def trace_table(trace: np.ndarray, names=("e-", "e+", "gamma")) -> str:
 def leaf_address(layout: str, i: int, f: int, cap: int) -> int:
     """Byte address of leaf f of track i (same mapping as the device layout layer)."""
     _, off, size = LEAVES[f]
+    if layout == "hotcold":  # hot 52 bytes AoSoA-32, cold fields SoA after them
+        if off < 52:
+            return (i // 32) * 52 * 32 + off * 32 + size * (i % 32)
+        return 52 * cap + (off - 52) * cap + 4 * i
     n = {"aos": 1, "soa": cap, "aosoa8": 8, "aosoa16": 16, "aosoa32": 32, "aosoa64": 64,
          "aosoa128": 128}[layout]
     return (i // n) * 64 * n + off * n + size * (i % n)

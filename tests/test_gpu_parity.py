@@ -16,7 +16,7 @@ from parity import assert_strict_parity, ledger_residual, oracle_run, run_gpu
 pytestmark = pytest.mark.gpu
 
 FORMS = ["sparse", "dense"]
-LAYOUTS = ["aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128"]
+LAYOUTS = ["aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128", "hotcold"]
 DRIVERS = ["hostloop", "graph", "persistent"]
 
 

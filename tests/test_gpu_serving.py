@@ -55,3 +55,19 @@ def test_sparse_slot_reuse_keeps_slots_bounded(geom):
     assert np.all(np.abs(score - o["score"]) <= DEPOSIT_RTOL * np.abs(o["score"]) + 1e-9)
     tracks = int(o["tracks"].sum())
     assert sum(c["slot_high_water"]) < tracks / 4
+
+
+@pytest.mark.parametrize("driver", ["persistent", "hostloop"])
+def test_serving_count_log_wraps(geom, driver):
+    """A serving context runs for as long as requests keep coming: its iteration count log
+    wraps instead of filling up (here 16 entries for a run of ~130 iterations)."""
+    from paper_2302_08252_gb300 import et
+    p = W.small_electrons(4, 1000.0)
+    ctx = et.make_context(geom, max_events=4, capacity_log2=16, form=et.FORM_DENSE,
+                          layout="aos", driver=driver, serving=True, max_iters=16)
+    et.et_inject(ctx, p)
+    tot = et.et_run_until_empty(ctx)
+    assert tot["iterations"] > 16
+    o = oracle_run(geom, p, 4, idlog=False)
+    assert et.et_read_counters(ctx)["steps"] == [int(x) for x in o["steps"]]
+    assert sorted(int(e) for e in et.et_poll_completed(ctx)) == [0, 1, 2, 3]

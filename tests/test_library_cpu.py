@@ -99,6 +99,23 @@ def test_aosoa128_needs_a_full_block(libet):
     cfg.block_size = 256
     h = ctypes.c_void_p()
     assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
-    cfg.layout = 7            # no such layout
+    cfg.layout = 8            # no such layout
     cfg.capacity_log2 = 10
     assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
+
+
+@pytest.mark.parametrize("layout", ["aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64",
+                                    "aosoa128", "hotcold"])
+def test_layout_mappings_tile_the_buffer(layout):
+    """Every layout places the 15 leaves of `cap` records at distinct, naturally aligned
+    byte ranges that exactly tile the cap * 64-byte buffer (the address formulas the
+    device layout layer and the heatmap plotter share in form)."""
+    from paper_2302_08252_gb300 import heatmap
+    cap = 256
+    used = np.zeros(cap * 64, dtype=np.int32)
+    for i in range(cap):
+        for f, (_, _, size) in enumerate(heatmap.LEAVES):
+            a = heatmap.leaf_address(layout, i, f, cap)
+            assert a % size == 0 and 0 <= a and a + size <= cap * 64
+            used[a:a + size] += 1
+    assert np.all(used == 1)
