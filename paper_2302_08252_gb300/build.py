@@ -35,7 +35,8 @@ FAST = ["-ftz=false"]
 
 
 def _sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)) + [os.path.join(INC, "et.h")]
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)) + sorted(
+        os.path.join(INC, f) for f in os.listdir(INC))
 
 
 def _fingerprint() -> str:

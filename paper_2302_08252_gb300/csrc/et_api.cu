@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "et.h"
+#include "et_debug.h"
 #include "kernels.cuh"
 #include "registry.h"
 
@@ -158,6 +159,29 @@ static et_status launch(et_ctx* c, const void* fn, int grid, int block, size_t s
   CUDA_TRY(c, cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, c->stream));
   c->launches += 1;
   return ET_OK;
+}
+
+// One thread per input: the primitives exactly as the step kernels use them.
+__global__ void k_debug_eval(int what, const void* in, void* out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (what == ET_EVAL_PHILOX) {
+    const uint32_t* c = static_cast<const uint32_t*>(in) + 6 * i;
+    const uint4 r = philox(c[0], c[1], c[2], c[3], c[4], c[5]);
+    uint32_t* o = static_cast<uint32_t*>(out) + 4 * i;
+    o[0] = r.x; o[1] = r.y; o[2] = r.z; o[3] = r.w;
+  } else if (what == ET_EVAL_U01) {
+    static_cast<float*>(out)[i] = u01(static_cast<const uint32_t*>(in)[i]);
+  } else if (what == ET_EVAL_LOG) {
+    static_cast<float*>(out)[i] = s_log(static_cast<const float*>(in)[i]);
+  } else if (what == ET_EVAL_EXP) {
+    static_cast<float*>(out)[i] = s_exp(static_cast<const float*>(in)[i]);
+  } else {
+    float sn, cs;
+    s_sincos2pi(static_cast<const float*>(in)[i], &sn, &cs);
+    static_cast<float*>(out)[2 * i] = sn;
+    static_cast<float*>(out)[2 * i + 1] = cs;
+  }
 }
 
 extern "C" {
@@ -864,7 +888,7 @@ et_status et_read_timing(et_ctx* c, double* ms_total, uint64_t* launches) {
   return ET_OK;
 }
 
-// Profiling hooks (not in et.h): per-iteration start times of the persistent driver.
+// Profiling hooks (et_debug.h): per-iteration start times of the persistent driver.
 et_status et_debug_iteration_times(et_ctx* c, int enable) {
   if (!c) return ET_ERR_INVALID;
   if (enable && !c->d_iter_ns) {
@@ -888,12 +912,25 @@ et_status et_debug_read_iteration_times(et_ctx* c, uint64_t* out, uint64_t cap, 
   return ET_OK;
 }
 
-// Test hooks (not in et.h): bounded-wait fault injection for the persistent driver.
+// Test hooks (et_debug.h): bounded-wait fault injection for the persistent driver.
 et_status et_debug_set_barrier_fault(et_ctx* c, int skip_block, uint64_t timeout_ns) {
   if (!c) return ET_ERR_INVALID;
   c->fault_skip_block = skip_block;
   if (timeout_ns) c->args.timeout_ns = timeout_ns;
   return ET_OK;
+}
+
+
+// Test hook (et_debug.h): the device primitives on a batch of inputs.
+et_status et_debug_eval(int what, const void* in, void* out, size_t n, void* stream) {
+  if (what < ET_EVAL_PHILOX || what > ET_EVAL_SINCOS2PI || (n && (!in || !out)))
+    return ET_ERR_INVALID;
+  if (n == 0) return ET_OK;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  k_debug_eval<<<grid, 256, 0, s>>>(what, in, out, n);
+  if (cudaGetLastError() != cudaSuccess) return ET_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? ET_OK : ET_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -108,6 +108,7 @@ def _load():
                                   vp, vp, vp, C.c_size_t, C.c_uint64, C.c_uint32, vp, vp,
                                   C.POINTER(C.c_uint64), vp, C.c_char_p, C.c_size_t], st),
         "et_debug_set_barrier_fault": ([vp, C.c_int, C.c_uint64], st),
+        "et_debug_eval": ([C.c_int, vp, vp, C.c_size_t, vp], st),
         "et_debug_iteration_times": ([vp, C.c_int], st),
         "et_debug_read_iteration_times": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
     }
@@ -163,9 +164,12 @@ def _torch_callbacks():
 def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_STRICT,
               driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
               instrument=False, id_log=False, id_log_capacity=0, stream=None,
-              use_torch_allocator=True, serving=False, reuse_slots=False) -> Context:
+              use_torch_allocator=True, serving=False, reuse_slots=False,
+              allocator=None) -> Context:
     """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
-    torch's current stream."""
+    torch's current stream.  allocator: optional (alloc(nbytes, stream) -> int address,
+    free(address)) pair of Python callables for the library's device buffers; default
+    PyTorch's caching allocator."""
     import torch
     if not torch.cuda.is_available():
         raise EtError(ET_ERR_CUDA, "no CUDA device")
@@ -192,7 +196,18 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
     cfg.serving = int(bool(serving))
     cfg.reuse_slots = int(bool(reuse_slots))
     cbs = None
-    if use_torch_allocator:
+    if allocator is not None:
+        fa, ff = allocator
+
+        def alloc(nbytes, stream, user):
+            try:
+                return fa(int(nbytes), int(stream or 0))
+            except Exception:
+                return None
+
+        cbs = (ALLOC_FN(alloc), FREE_FN(lambda ptr, user: ff(int(ptr))))
+        cfg.alloc, cfg.free = cbs
+    elif use_torch_allocator:
         cbs = _torch_callbacks()
         cfg.alloc, cfg.free = cbs
     h = C.c_void_p()
@@ -437,3 +452,19 @@ def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) 
     t = tables if tables is not None else et_build_toy_tables()
     et_load_tables(ctx, t["sigma"], t["dedx"], t["log_emin"], t["inv_dlog"])
     return ctx
+
+
+EVAL_PHILOX, EVAL_U01, EVAL_LOG, EVAL_EXP, EVAL_SINCOS2PI = range(5)
+
+
+def et_debug_eval(what: int, inputs, outputs):
+    """Evaluate a device primitive (et_debug.h) on CUDA tensors: inputs uint32 [n, 6]
+    (Philox), uint32 [n] (u01) or float32 [n]; outputs sized accordingly."""
+    import torch
+    n = inputs.shape[0]
+    st = lib.et_debug_eval(what, C.c_void_p(inputs.data_ptr()), C.c_void_p(outputs.data_ptr()), n,
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != ET_OK:
+        raise EtError(st, "et_debug_eval")
+    return outputs
+
