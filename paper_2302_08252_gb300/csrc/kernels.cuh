@@ -585,41 +585,53 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Returns false if this block gave up waiting (status ST_TIMEOUT is then set).  `gen` is
-// thread 0's copy of the barrier generation (read once at kernel start: it cannot move
-// before every block has arrived at the first barrier); `rings`: the sparse form's slot
-// reuse rings move their boundary here.
+// Grid barrier of the persistent kernel.  Every block's thread 0 announces its arrival
+// with a release reduction on a counter that only grows (nblocks per barrier); block 0's
+// thread 0 waits (acquire) until the counter reaches nblocks * (gen + 1), takes the
+// status snapshot that every block's next decision uses, moves the sparse form's
+// slot-reuse ring boundary (`rings`) while every other block waits, and publishes the
+// next generation (release); the others wait (acquire) for it.  `gen` is thread 0's
+// copy of the generation, read once at kernel start (it cannot move before every block
+// has arrived at the first barrier).  Every wait is bounded: on timeout the block sets
+// ST_TIMEOUT and the function returns false.
 static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long timeout_ns,
                                  uint32_t* snap_status, uint32_t& gen, bool rings) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> g_ref(c->bar_gen);
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> cnt(c->bar_count);
-    cuda::atomic_ref<uint32_t, cuda::thread_scope_device> st(c->status);
     const uint32_t g = gen;
-    __threadfence();  // this block's writes before the arrival
-    const uint32_t arrived = cnt.fetch_add(1u, cuda::memory_order_relaxed);
     int ok = 1;
-    if (arrived == nblocks - 1) {
-      __threadfence();  // the other blocks' writes (status bits, rings) before the reads below
-      cnt.store(0u, cuda::memory_order_relaxed);
-      *snap_status = st.load(cuda::memory_order_relaxed);
-      if (rings) free_ring_boundary(c);  // every other block is waiting: no slot is being taken
-      __threadfence();
-      g_ref.store(g + 1u, cuda::memory_order_relaxed);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (g_ref.load(cuda::memory_order_relaxed) == g) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&c->bar_count) : "memory");
+    const unsigned long long t0 = global_ns();
+    if (blockIdx.x == 0) {
+      const uint32_t target = nblocks * (g + 1u);
+      for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&c->bar_count) : "memory");
+        if ((int32_t)(v - target) >= 0) break;
         if (global_ns() - t0 > timeout_ns) {
-          st.fetch_or(ST_TIMEOUT, cuda::memory_order_relaxed);
+          atomicOr(&c->status, ST_TIMEOUT);
           ok = 0;
           break;
         }
-        __nanosleep(32);
+      }
+      if (ok) {
+        *snap_status = *(volatile uint32_t*)&c->status;
+        if (rings) free_ring_boundary(c);
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&c->bar_gen), "r"(g + 1u) : "memory");
+      }
+    } else {
+      for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&c->bar_gen) : "memory");
+        if (v != g) break;
+        if (global_ns() - t0 > timeout_ns) {
+          atomicOr(&c->status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();  // the other blocks' writes before this block's next reads
     gen = g + 1u;
     ok_s = ok;
   }
@@ -664,7 +676,6 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       c->run_sec0[t] = c->secondaries[t];
     }
   }
-  uint32_t status0 = *(volatile uint32_t*)&c->status;
   uint32_t bar_gen = threadIdx.x == 0 ? *(volatile uint32_t*)&c->bar_gen : 0u;
   bool first = true;
   Tally tl;  // flushed when the loop ends
@@ -673,7 +684,10 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
     if (threadIdx.x == 0) {
       const uint32_t cur = it % 3;
       for (int t = 0; t < 3; ++t) s_n[t] = __ldcg(&c->cnt[cur][cw(t)]);
-      const uint32_t st = first ? status0 : *snap;
+      // the first decision uses only what the launch started with (the same in every
+      // block: a block that starts late must not see a status bit set by another block's
+      // first iteration); later ones use the snapshot taken at the barrier
+      const uint32_t st = first ? 0u : *(volatile uint32_t*)snap;
       s_stop = (s_n[0] + s_n[1] + s_n[2] == 0) || it >= stop_iter || st != 0;
     }
     __syncthreads();
