@@ -52,7 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--form", default="dense", choices=["dense", "sparse"])
     ap.add_argument("--layout", default="aosoa32", choices=["aos", "soa", "aosoa8", "aosoa16", "aosoa32",
                                                          "aosoa64", "aosoa128", "hotcold"])
-    ap.add_argument("--driver", default="persistent", choices=["hostloop", "graph", "persistent"])
+    ap.add_argument("--driver", default="persistent", choices=["hostloop", "graph", "persistent", "hybrid"])
     ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--capacity-log2", type=int, default=22)

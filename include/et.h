@@ -65,7 +65,9 @@ enum {
   ET_LAYOUT_HOTCOLD = 7  /* hot 52 bytes AoSoA-32, cold time/length/flags SoA */
 };
 enum { ET_MODE_STRICT = 0, ET_MODE_FAST = 1 };
-enum { ET_DRIVER_HOSTLOOP = 0, ET_DRIVER_GRAPH = 1, ET_DRIVER_PERSISTENT = 2 };
+/* HYBRID: the persistent kernel while fewer than cfg.hybrid_tracks tracks are active,
+ * the CUDA graph of per-type step kernels while at least that many are. */
+enum { ET_DRIVER_HOSTLOOP = 0, ET_DRIVER_GRAPH = 1, ET_DRIVER_PERSISTENT = 2, ET_DRIVER_HYBRID = 3 };
 
 /* Device allocator callbacks: return NULL on failure. */
 typedef void* (*et_alloc_fn)(size_t bytes, void* stream, void* user);
@@ -94,6 +96,7 @@ typedef struct {
                                instead of filling up */
   int32_t reuse_slots;      /* sparse form: 1 = slots of dead tracks are reused (from the next
                                iteration on); 0 = never reused (the plain single buffer) */
+  uint32_t hybrid_tracks;   /* ET_DRIVER_HYBRID: the switch-over population (0 = 2^21) */
 } et_config;
 
 /* Create a context (allocates the track buffers).  *out is NULL on failure. */

@@ -3,6 +3,8 @@ per-type launch split for a workload by timing the candidates on a sample of it.
 
 Launch splits:
   persistent   one cooperative kernel runs all particle types and all iterations
+  hybrid       the persistent kernel for iterations below 2^21 active tracks, the graph
+               (below) for the larger ones
   graph        one step kernel per particle type per iteration, captured once in a CUDA
                graph whose WHILE condition is set from the device
   hostloop     one step kernel per particle type per iteration, launched from the host
@@ -24,7 +26,7 @@ import numpy as np
 
 LAYOUTS = ("aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64", "aosoa128", "hotcold")
 BLOCKS = (64, 128, 256)
-DRIVERS = ("persistent", "graph", "hostloop")
+DRIVERS = ("persistent", "graph", "hostloop", "hybrid")
 
 
 def sample_events(primaries: np.ndarray, n_events: int, seed: int = 7) -> np.ndarray:

@@ -123,6 +123,8 @@ struct Args {
   uint32_t* counts_log;         // [max_iters][3]
   uint32_t max_iters;
   uint32_t iter_log_wrap;        // serving: the count log is a ring (entry it % max_iters)
+  uint32_t hybrid_t;             // hybrid driver: the persistent kernel stops before an iteration
+                                 // with this many tracks, the graph before one with fewer (0: off)
   uint32_t n_slabs;
   double* score;                // [max_events][n_slabs]
   double* ledger;               // [max_events][5]: injected, cut, escaped, mass_created, mass_consumed

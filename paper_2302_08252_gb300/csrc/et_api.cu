@@ -198,7 +198,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   if (k.capacity_log2 < 6 || k.capacity_log2 > 28 || (k.form != 0 && k.form != 1) ||
       k.layout < 0 || k.layout >= N_LAYOUTS || (k.mode != 0 && k.mode != 1) || k.driver < 0 ||
       (k.layout == LAYOUT_AOSOA128 && k.capacity_log2 < 7) ||
-      k.driver > 2 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
+      k.driver > 3 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
       k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) ||
       ((k.alloc == nullptr) != (k.free == nullptr)))
     return ET_ERR_INVALID;
@@ -241,6 +241,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   a.counts_log = (uint32_t*)dalloc(c, (size_t)k.max_iters * 3u * 4u);
   a.max_iters = k.max_iters;
   a.iter_log_wrap = k.serving ? 1u : 0u;
+  a.hybrid_t = k.driver == ET_DRIVER_HYBRID ? (k.hybrid_tracks ? k.hybrid_tracks : 1u << 21) : 0u;
   a.max_events = k.max_events;
   a.ledger = (double*)dalloc(c, (size_t)k.max_events * 5u * 8u);
   if (!a.ctl || !a.counts_log || !a.ledger) return fail(c, ET_ERR_NOMEM, "control block");
@@ -626,24 +627,72 @@ static et_status build_graph(et_ctx* c) {
   return ET_OK;
 }
 
+static et_status launch_persistent(et_ctx* c, uint32_t rel) {
+  c->h_stop[1] = rel;
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_rel, c->h_stop + 1, 4, cudaMemcpyHostToDevice, c->stream));
+  int fault = c->fault_skip_block;
+  void* params[] = {(void*)&c->args, (void*)&fault};
+  const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+  EventPair* ev = timing_begin(c);
+  CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block), params,
+                                          c->smem_all, c->stream));
+  timing_end(c, ev);
+  c->launches += 1;
+  return ET_OK;
+}
+
+static et_status launch_graph(et_ctx* c, uint32_t stop_iter) {
+  c->h_stop[0] = stop_iter;
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
+  if (!c->gexec) {
+    et_status s = build_graph(c);
+    if (s != ET_OK) return s;
+  }
+  EventPair* ev = timing_begin(c);
+  CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+  timing_end(c, ev);
+  c->launches += 1;
+  return ET_OK;
+}
+
+// Hybrid driver: small iterations in the persistent kernel (one launch loops them on the
+// device), large ones in the graph of per-type step kernels; each launch stops where the
+// population crosses the threshold (the kernels check it), and runs at least one
+// iteration, so every round of this loop makes progress.
+static et_status run_hybrid(et_ctx* c, uint64_t max_iters, et_iter_stats* totals,
+                            uint64_t* n_iters) {
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const DevCtl before = *c->h_ctl;
+  const uint32_t it0 = before.iter;
+  uint64_t lim64 = (uint64_t)it0 + max_iters;
+  const uint32_t lim = lim64 > 0xffffffffull ? 0xffffffffu : (uint32_t)lim64;
+  for (;;) {
+    const uint32_t it = c->h_ctl->iter;
+    const uint32_t* row = c->h_ctl->cnt[it % 3];
+    const uint64_t n = (uint64_t)row[0] + row[1] + row[2];
+    if (n == 0 || it >= lim) break;
+    s = n < c->args.hybrid_t ? launch_persistent(c, lim - it) : launch_graph(c, lim);
+    if (s != ET_OK) return s;
+    s = sync_ctl(c);
+    if (s != ET_OK) return s;
+  }
+  fill_stats(c, before, totals);
+  if (n_iters) *n_iters = c->h_ctl->iter - it0;
+  return ET_OK;
+}
+
 et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* totals,
                              uint64_t* n_iters) {
   if (!c) return ET_ERR_INVALID;
   if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (c->cfg.driver == ET_DRIVER_HYBRID) return run_hybrid(c, max_iters, totals, n_iters);
   if (c->cfg.driver == ET_DRIVER_PERSISTENT && max_iters > 0) {
     // one launch, one read-back: the kernel stops after max_iters iterations (or when no
     // track is left) and records its starting iteration and counters for the totals
-    c->h_stop[1] = max_iters > 0xffffffffull ? 0xffffffffu : (uint32_t)max_iters;
-    CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_rel, c->h_stop + 1, 4, cudaMemcpyHostToDevice, c->stream));
-    int fault = c->fault_skip_block;
-    void* params[] = {(void*)&c->args, (void*)&fault};
-    const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
-    EventPair* ev = timing_begin(c);
-    CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block), params,
-                                            c->smem_all, c->stream));
-    timing_end(c, ev);
-    c->launches += 1;
-    et_status s = sync_ctl(c);
+    et_status s = launch_persistent(c, max_iters > 0xffffffffull ? 0xffffffffu : (uint32_t)max_iters);
+    if (s != ET_OK) return s;
+    s = sync_ctl(c);
     if (s != ET_OK) return s;
     DevCtl before = *c->h_ctl;
     before.iter = c->h_ctl->run_iter0;
@@ -672,27 +721,14 @@ et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* total
         if (empty) break;
       }
     } else {
-      c->h_stop[0] = (uint32_t)lim;
-      CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
       if (c->cfg.driver == ET_DRIVER_GRAPH) {
-        if (!c->gexec) {
-          s = build_graph(c);
-          if (s != ET_OK) return s;
-        }
-        EventPair* ev = timing_begin(c);
-        CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
-        timing_end(c, ev);
-        c->launches += 1;
-      } else {
-        int fault = c->fault_skip_block;
-        void* params[] = {(void*)&c->args, (void*)&fault};
-        const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
-        EventPair* ev = timing_begin(c);
-        CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block), params,
-                                                c->smem_all, c->stream));
-        timing_end(c, ev);
-        c->launches += 1;
+        s = launch_graph(c, (uint32_t)lim);
+      } else {  // persistent with max_iters == 0 does not get here
+        c->h_stop[0] = (uint32_t)lim;
+        CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
+        s = launch_persistent(c, 0u);
       }
+      if (s != ET_OK) return s;
     }
   }
   s = sync_ctl(c);

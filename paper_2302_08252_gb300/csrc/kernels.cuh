@@ -575,7 +575,8 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
   for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
   c->iter = it + 1;
   const uint32_t left = c->cnt[nxt][0] + c->cnt[nxt][1] + c->cnt[nxt][2];
-  const bool stop = left == 0 || c->status != 0 || it + 1 >= c->stop_iter;
+  const bool stop = left == 0 || c->status != 0 || it + 1 >= c->stop_iter ||
+                    (a.hybrid_t != 0 && left < a.hybrid_t);
   c->done = stop ? 1u : 0u;
   if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
@@ -691,7 +692,8 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       // block: a block that starts late must not see a status bit set by another block's
       // first iteration); later ones use the snapshot taken at the barrier
       const uint32_t st = first ? 0u : *(volatile uint32_t*)snap;
-      s_stop = (s_n[0] + s_n[1] + s_n[2] == 0) || it >= stop_iter || st != 0;
+      const uint32_t tot = s_n[0] + s_n[1] + s_n[2];
+      s_stop = tot == 0 || it >= stop_iter || st != 0 || (a.hybrid_t != 0 && tot >= a.hybrid_t);
     }
     __syncthreads();
     first = false;

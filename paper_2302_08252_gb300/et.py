@@ -28,8 +28,8 @@ LAYOUT_AOS, LAYOUT_SOA, LAYOUT_AOSOA32, LAYOUT_AOSOA64, LAYOUT_AOSOA8, LAYOUT_AO
 LAYOUTS = {"aos": 0, "soa": 1, "aosoa32": 2, "aosoa64": 3, "aosoa8": 4, "aosoa16": 5,
            "aosoa128": 6, "hotcold": 7}
 MODE_STRICT, MODE_FAST = 0, 1
-DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT = range(3)
-DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2}
+DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT, DRIVER_HYBRID = range(4)
+DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2, "hybrid": 3}
 N_LEAVES = 15
 LEAF_NAMES = ("x", "y", "z", "dx", "dy", "dz", "ekin", "num_ia_left", "id", "event", "step",
               "slab", "time", "track_len", "flags")
@@ -52,7 +52,7 @@ class et_config(C.Structure):
                 ("instrument", C.c_int32), ("id_log", C.c_int32),
                 ("id_log_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("serving", C.c_int32), ("reuse_slots", C.c_int32)]
+                ("serving", C.c_int32), ("reuse_slots", C.c_int32), ("hybrid_tracks", C.c_uint32)]
 
 
 class et_iter_stats(C.Structure):
@@ -165,7 +165,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
               driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
               instrument=False, id_log=False, id_log_capacity=0, stream=None,
               use_torch_allocator=True, serving=False, reuse_slots=False,
-              allocator=None) -> Context:
+              allocator=None, hybrid_tracks=0) -> Context:
     """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
     torch's current stream.  allocator: optional (alloc(nbytes, stream) -> int address,
     free(address)) pair of Python callables for the library's device buffers; default
@@ -195,6 +195,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
     cfg.cuda_stream = s
     cfg.serving = int(bool(serving))
     cfg.reuse_slots = int(bool(reuse_slots))
+    cfg.hybrid_tracks = int(hybrid_tracks)
     cbs = None
     if allocator is not None:
         fa, ff = allocator

@@ -13,7 +13,7 @@ DEPOSIT_RTOL = 1e-6
 
 def run_gpu(geom, primaries, n_events, form="dense", layout="aos", driver="hostloop",
             capacity_log2=16, id_log=True, mode=0, seed=1, instrument=False, block_size=256,
-            id_log_capacity=None):
+            id_log_capacity=None, **ctx_kw):
     from paper_2302_08252_gb300 import et
     n_slabs = len(geom["thickness"])
     ctx = et.make_context(geom, max_events=n_events, capacity_log2=capacity_log2,
@@ -21,7 +21,7 @@ def run_gpu(geom, primaries, n_events, form="dense", layout="aos", driver="hostl
                           layout=layout, driver=driver, mode=mode, seed=seed,
                           id_log=id_log,
                           id_log_capacity=(id_log_capacity or (1 << capacity_log2) * 8) if id_log else 0,
-                          instrument=instrument, block_size=block_size)
+                          instrument=instrument, block_size=block_size, **ctx_kw)
     et.et_inject(ctx, primaries)
     tot = et.et_run_until_empty(ctx)
     score, ledger = et.et_read_scoring_all(ctx, n_events, n_slabs)

@@ -11,9 +11,9 @@ def test_selection_picks_fastest_and_covers_all_candidates():
     cost = {"aos": 3.0, "soa": 2.0, "aosoa8": 1.8, "aosoa16": 1.4, "aosoa32": 1.0,
             "aosoa64": 1.5, "aosoa128": 1.7, "hotcold": 1.2}
     timer = lambda layout, block, driver: cost[layout] + {64: 0.3, 128: 0.1, 256: 0.2}[block] + \
-        {"persistent": 0.0, "graph": 1.0, "hostloop": 2.0}[driver]
+        {"persistent": 0.0, "graph": 1.0, "hostloop": 2.0, "hybrid": 0.5}[driver]
     r = autotune.autotune(None, W.uneven_events(8, 5), 8, timer=timer)
-    assert len(r["table"]) == 8 * 3 * 3
+    assert len(r["table"]) == 8 * 3 * 4
     assert r["best"]["layout"] == "aosoa32" and r["best"]["block_size"] == 128
     assert r["best"]["driver"] == "persistent"
 

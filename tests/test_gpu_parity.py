@@ -82,6 +82,25 @@ def test_full_jittered_electrons(geom):
     assert ledger_residual(g["ledger"]) < 1e-12
 
 
+@pytest.mark.parametrize("threshold", [1, 300, 4000])
+def test_hybrid_driver_bit_exact(geom, small_ref, threshold):
+    """Persistent kernel below the threshold, graph of per-type kernels above it, switching
+    back and forth as the showers grow and die out: the same histories."""
+    from paper_2302_08252_gb300 import et
+    p, o = small_ref
+    ctx_kw = dict(hybrid_tracks=threshold)
+    g = run_gpu(geom, p, 16, form="dense", layout="aosoa32", driver="hybrid", **ctx_kw)
+    assert_strict_parity(g, o)
+
+
+def test_hybrid_driver_full_jittered(geom):
+    p = W.jittered_electrons()
+    o = oracle_run(geom, p, 1000, nthreads=16)
+    g = run_gpu(geom, p, 1000, form="dense", layout="aosoa32", driver="hybrid",
+                capacity_log2=21, id_log=True, id_log_capacity=1 << 25)
+    assert_strict_parity(g, o)
+
+
 def test_empty_run_and_invalid_input(geom):
     from paper_2302_08252_gb300 import et
     ctx = et.make_context(geom, max_events=4, capacity_log2=10)
