@@ -117,7 +117,6 @@ struct IdRec {
 struct Args {
   char* trk[NTYPES][2];         // dense: [type][half]; sparse: [type][0]
   uint32_t* idx[NTYPES][2];     // sparse: slot lists [type][parity]
-  uint32_t* freelist[NTYPES];   // sparse: free-slot stacks (NULL: slots are never reused)
   uint32_t cap;                 // slots per buffer
   DevCtl* ctl;
   uint32_t* counts_log;         // [max_iters][3]

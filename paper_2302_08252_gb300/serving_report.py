@@ -24,13 +24,15 @@ FORMS = {"tuned": ("dense", "aosoa32", "persistent"), "plain": ("sparse", "aos",
 
 
 def run(rate: float, n_events: int, max_primaries: int, warmup_frac: float, form_key: str,
-        capacity_log2: int = 24) -> dict:
+        capacity_log2: int = 24, tuned_driver: str = "persistent", iters_per_round: int = 8) -> dict:
     form, layout, driver = FORMS[form_key]
+    if form_key == "tuned":
+        driver = tuned_driver
     geom = W.calorimeter()
     reqs = serving.poisson_requests(rate, n_events, max_primaries=max_primaries)
     srv = serving.Server(geom, form=form, layout=layout, driver=driver,
                          capacity_log2=capacity_log2, max_events=max(1024, n_events),
-                         iters_per_round=8)
+                         iters_per_round=iters_per_round)
     st = srv.serve(reqs)
     skip = int(warmup_frac * n_events)
     kept = sorted(st.results, key=lambda r: r.arrival)[skip:]
@@ -53,12 +55,16 @@ def main(argv=None):
     ap.add_argument("--max-primaries", type=int, default=1000)
     ap.add_argument("--warmup-frac", type=float, default=0.1)
     ap.add_argument("--forms", nargs="+", default=["tuned", "plain"])
+    ap.add_argument("--tuned-driver", default="persistent",
+                    choices=["persistent", "graph", "hostloop", "hybrid"])
+    ap.add_argument("--iters-per-round", type=int, default=8)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     rows = []
     for rate in a.rates:
         for fk in a.forms:
-            r = run(rate, a.events, a.max_primaries, a.warmup_frac, fk)
+            r = run(rate, a.events, a.max_primaries, a.warmup_frac, fk,
+                    tuned_driver=a.tuned_driver, iters_per_round=a.iters_per_round)
             r["which"] = fk
             rows.append(r)
             print(json.dumps(r), flush=True)
