@@ -237,6 +237,23 @@ typedef struct {
 } et_counters;
 et_status et_read_counters(et_ctx* ctx, et_counters* out);
 
+/*
+ * Checkpoint / resume.  et_snapshot copies the state of a context between iterations
+ * into host memory: control block and counters, the live part of the track arrays
+ * (dense: the current buffer's first n records per type; sparse: the slot array, the
+ * current slot list and the reuse rings), scores, ledgers, the iteration log, the
+ * serving counters, the death log and the instrumentation counts.  et_snapshot_size
+ * gives the bytes it needs (cap); written receives the bytes written.  et_restore
+ * loads a snapshot into a context created with the same configuration (ET_ERR_INVALID
+ * otherwise, or for a damaged snapshot) after loading the same geometry and tables;
+ * every draw is keyed by (event, id, step), so the restored context follows exactly the
+ * histories the original would have.  Completed events reported before the snapshot
+ * are not reported again.  All three synchronise the stream.
+ */
+et_status et_snapshot_size(et_ctx* ctx, uint64_t* bytes);
+et_status et_snapshot(et_ctx* ctx, void* out, uint64_t cap, uint64_t* written);
+et_status et_restore(et_ctx* ctx, const void* in, uint64_t n);
+
 /* Forget all tracks, scores, ledgers, logs and counters (buffers stay allocated). */
 et_status et_reset(et_ctx* ctx);
 

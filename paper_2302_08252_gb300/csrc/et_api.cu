@@ -969,4 +969,192 @@ et_status et_debug_eval(int what, const void* in, void* out, size_t n, void* str
   return cudaStreamSynchronize(s) == cudaSuccess ? ET_OK : ET_ERR_CUDA;
 }
 
+
+// ---- checkpoint / resume ----
+// A snapshot is a header (the configuration it belongs to) followed by tagged sections:
+// the control block, the live part of the track arrays (dense: the current half; sparse:
+// the slot array, the current slot list and the reuse rings), scores, ledgers, the
+// iteration log, the serving counters, the death log and the instrumentation counts.
+// Every random draw is keyed by (event, id, step), so a restored context continues with
+// exactly the histories the original would have followed.
+namespace {
+struct SnapHeader {
+  char magic[8];
+  uint32_t version, form, layout, capacity_log2, mode, max_events, max_iters, n_slabs;
+  uint32_t serving, reuse_slots, id_log, instrument;
+  uint64_t id_log_capacity, seed, n_sections;
+};
+struct SnapSection {
+  uint32_t tag, index;
+  uint64_t bytes;
+};
+enum : uint32_t { SN_CTL = 1, SN_TRK, SN_IDX, SN_FREE, SN_SCORE, SN_LEDGER, SN_COUNTS, SN_LIVE,
+                  SN_DONE, SN_IDLOG, SN_TRACE, SN_HEAT };
+constexpr char kSnapMagic[8] = {'E', 'T', 'S', 'N', 'A', 'P', '1', 0};
+
+struct SnapItem {
+  uint32_t tag, index;
+  void* dev;
+  uint64_t bytes;
+};
+
+// bytes of a track array that hold its first n records
+uint64_t record_prefix(int layout, uint64_t n, uint64_t cap) {
+  const uint64_t lanes = layout == ET_LAYOUT_AOS ? 1 : layout == ET_LAYOUT_AOSOA8 ? 8
+                         : layout == ET_LAYOUT_AOSOA16 ? 16 : layout == ET_LAYOUT_AOSOA32 ? 32
+                         : layout == ET_LAYOUT_AOSOA64 ? 64 : layout == ET_LAYOUT_AOSOA128 ? 128 : 0;
+  if (lanes == 0) return cap * 64u;  // SoA-like layouts spread every record over the array
+  const uint64_t blocks = (n + lanes - 1) / lanes;
+  return std::min(cap, blocks * lanes) * 64u;
+}
+}  // namespace
+
+static std::vector<SnapItem> snapshot_items(et_ctx* c) {
+  std::vector<SnapItem> v;
+  Args& a = c->args;
+  const DevCtl& h = *c->h_ctl;
+  const uint32_t it = h.iter, cur = it % 3, half = it & 1u;
+  v.push_back({SN_CTL, 0, c->d_ctl, sizeof(DevCtl)});
+  for (int t = 0; t < NTYPES; ++t) {
+    if (c->dense) {
+      v.push_back({SN_TRK, (uint32_t)(2 * t + half), a.trk[t][half],
+                   record_prefix(c->cfg.layout, h.cnt[cur][cw(t)], c->cap)});
+    } else {
+      v.push_back({SN_TRK, (uint32_t)(2 * t), a.trk[t][0], (uint64_t)c->cap * 64u});
+      v.push_back({SN_IDX, (uint32_t)(2 * t + half), a.idx[t][half], (uint64_t)h.cnt[cur][cw(t)] * 4u});
+      if (a.free_ring[t]) v.push_back({SN_FREE, (uint32_t)t, a.free_ring[t], (uint64_t)c->cap * 4u});
+    }
+    for (int hh = 0; hh < 2; ++hh)
+      if (a.heat[t][hh]) v.push_back({SN_HEAT, (uint32_t)(2 * t + hh), a.heat[t][hh], (uint64_t)c->cap * 64u});
+  }
+  v.push_back({SN_SCORE, 0, a.score, (uint64_t)a.max_events * a.n_slabs * 8u});
+  v.push_back({SN_LEDGER, 0, a.ledger, (uint64_t)a.max_events * 5u * 8u});
+  v.push_back({SN_COUNTS, 0, a.counts_log, (uint64_t)a.max_iters * 12u});
+  if (a.live) {
+    v.push_back({SN_LIVE, 0, a.live, (uint64_t)a.max_events * 4u});
+    v.push_back({SN_DONE, 0, a.done_ring, (uint64_t)a.done_cap * 4u});
+  }
+  if (a.idlog) {
+    const uint64_t m = std::min<uint64_t>(h.idlog_n, a.idlog_cap);
+    v.push_back({SN_IDLOG, 0, a.idlog, m * sizeof(IdRec)});
+  }
+  if (a.trace) v.push_back({SN_TRACE, 0, a.trace, 3u * NLEAF * 2u * 8u});
+  return v;
+}
+
+static SnapHeader snapshot_header(const et_ctx* c, uint64_t n_sections) {
+  SnapHeader hd;
+  memset(&hd, 0, sizeof hd);
+  memcpy(hd.magic, kSnapMagic, 8);
+  hd.version = 1;
+  hd.form = (uint32_t)c->cfg.form;
+  hd.layout = (uint32_t)c->cfg.layout;
+  hd.capacity_log2 = c->cfg.capacity_log2;
+  hd.mode = (uint32_t)c->cfg.mode;
+  hd.max_events = c->cfg.max_events;
+  hd.max_iters = c->cfg.max_iters;
+  hd.n_slabs = c->args.n_slabs;
+  hd.serving = (uint32_t)c->cfg.serving;
+  hd.reuse_slots = (uint32_t)c->cfg.reuse_slots;
+  hd.id_log = (uint32_t)c->cfg.id_log;
+  hd.instrument = (uint32_t)c->cfg.instrument;
+  hd.id_log_capacity = c->cfg.id_log_capacity;
+  hd.seed = c->cfg.seed;
+  hd.n_sections = n_sections;
+  return hd;
+}
+
+et_status et_snapshot_size(et_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  uint64_t n = sizeof(SnapHeader);
+  for (const SnapItem& it : snapshot_items(c)) n += sizeof(SnapSection) + it.bytes;
+  *bytes = n;
+  return ET_OK;
+}
+
+et_status et_snapshot(et_ctx* c, void* out, uint64_t cap, uint64_t* written) {
+  if (!c || !out) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  et_status s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  const std::vector<SnapItem> items = snapshot_items(c);
+  uint64_t need = sizeof(SnapHeader);
+  for (const SnapItem& it : items) need += sizeof(SnapSection) + it.bytes;
+  if (cap < need) return fail(c, ET_ERR_CAPACITY, "snapshot needs %llu bytes", (unsigned long long)need);
+  unsigned char* p = static_cast<unsigned char*>(out);
+  const SnapHeader hd = snapshot_header(c, items.size());
+  memcpy(p, &hd, sizeof hd);
+  p += sizeof hd;
+  for (const SnapItem& it : items) {
+    const SnapSection sec{it.tag, it.index, it.bytes};
+    memcpy(p, &sec, sizeof sec);
+    p += sizeof sec;
+    if (it.bytes) CUDA_TRY(c, cudaMemcpyAsync(p, it.dev, it.bytes, cudaMemcpyDeviceToHost, c->stream));
+    p += it.bytes;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (written) *written = need;
+  return ET_OK;
+}
+
+et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
+  if (!c || !in) return ET_ERR_INVALID;
+  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (n < sizeof(SnapHeader)) return fail(c, ET_ERR_INVALID, "snapshot too short");
+  SnapHeader hd;
+  memcpy(&hd, in, sizeof hd);
+  const SnapHeader mine = snapshot_header(c, hd.n_sections);
+  if (memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1)
+    return fail(c, ET_ERR_INVALID, "not a snapshot of this library");
+  if (memcmp(&hd, &mine, sizeof hd) != 0)
+    return fail(c, ET_ERR_INVALID, "snapshot of a context with another configuration");
+  et_status s = et_reset(c);
+  if (s != ET_OK) return s;
+  // find the device buffer of each section in this context
+  Args& a = c->args;
+  const unsigned char* p = static_cast<const unsigned char*>(in) + sizeof hd;
+  const unsigned char* end = static_cast<const unsigned char*>(in) + n;
+  for (uint64_t k = 0; k < hd.n_sections; ++k) {
+    if ((uint64_t)(end - p) < sizeof(SnapSection)) return fail(c, ET_ERR_INVALID, "snapshot truncated");
+    SnapSection sec;
+    memcpy(&sec, p, sizeof sec);
+    p += sizeof sec;
+    if ((uint64_t)(end - p) < sec.bytes) return fail(c, ET_ERR_INVALID, "snapshot truncated");
+    void* dev = nullptr;
+    uint64_t limit = 0;
+    const uint32_t t = sec.index / 2, hh = sec.index % 2;
+    switch (sec.tag) {
+      case SN_CTL: dev = c->d_ctl; limit = sizeof(DevCtl); break;
+      case SN_TRK: if (t < 3) { dev = a.trk[t][c->dense ? hh : 0]; limit = (uint64_t)c->cap * 64u; } break;
+      case SN_IDX: if (t < 3 && !c->dense) { dev = a.idx[t][hh]; limit = (uint64_t)c->cap * 4u; } break;
+      case SN_FREE: if (sec.index < 3) { dev = a.free_ring[sec.index]; limit = (uint64_t)c->cap * 4u; } break;
+      case SN_HEAT: if (t < 3) { dev = a.heat[t][hh]; limit = (uint64_t)c->cap * 64u; } break;
+      case SN_SCORE: dev = a.score; limit = (uint64_t)a.max_events * a.n_slabs * 8u; break;
+      case SN_LEDGER: dev = a.ledger; limit = (uint64_t)a.max_events * 40u; break;
+      case SN_COUNTS: dev = a.counts_log; limit = (uint64_t)a.max_iters * 12u; break;
+      case SN_LIVE: dev = a.live; limit = (uint64_t)a.max_events * 4u; break;
+      case SN_DONE: dev = a.done_ring; limit = (uint64_t)a.done_cap * 4u; break;
+      case SN_IDLOG: dev = a.idlog; limit = a.idlog_cap * sizeof(IdRec); break;
+      case SN_TRACE: dev = a.trace; limit = 3u * NLEAF * 2u * 8u; break;
+      default: break;
+    }
+    if (!dev || sec.bytes > limit) return fail(c, ET_ERR_INVALID, "snapshot section %u/%u does not fit", sec.tag, sec.index);
+    if (sec.bytes) CUDA_TRY(c, cudaMemcpyAsync(dev, p, sec.bytes, cudaMemcpyHostToDevice, c->stream));
+    p += sec.bytes;
+  }
+  // the grid barrier restarts from zero (the grid may differ on another GPU); launch-local
+  // fields are set by the next run
+  DevCtl* d = c->d_ctl;
+  CUDA_TRY(c, cudaMemsetAsync(&d->bar_count, 0, sizeof(uint32_t) * 2, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(d->grab, 0, sizeof d->grab, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  s = sync_ctl(c);
+  if (s != ET_OK) return s;
+  c->done_read = c->h_ctl->n_done;  // completions before the snapshot were already reported
+  return ET_OK;
+}
+
 }  // extern "C"

@@ -100,6 +100,9 @@ def _load():
         "et_read_heatmap": ([vp, C.c_uint32, C.c_uint32, vp, C.c_uint64], st),
         "et_read_counters": ([vp, C.POINTER(et_counters)], st),
         "et_reset": ([vp], st),
+        "et_snapshot_size": ([vp, C.POINTER(C.c_uint64)], st),
+        "et_snapshot": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
+        "et_restore": ([vp, vp, C.c_uint64], st),
         "et_poll_completed": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
         "et_release_event": ([vp, C.c_uint32], st),
         "et_set_timing": ([vp, C.c_int], st),
@@ -468,4 +471,19 @@ def et_debug_eval(what: int, inputs, outputs):
     if st != ET_OK:
         raise EtError(st, "et_debug_eval")
     return outputs
+
+
+def et_snapshot(ctx) -> bytes:
+    """The context's state between iterations (see et.h) as bytes."""
+    n = C.c_uint64()
+    _check(ctx, lib.et_snapshot_size(ctx.handle, C.byref(n)))
+    buf = np.empty(n.value, dtype=np.uint8)
+    w = C.c_uint64()
+    _check(ctx, lib.et_snapshot(ctx.handle, _p(buf), n.value, C.byref(w)))
+    return buf[: w.value].tobytes()
+
+
+def et_restore(ctx, snapshot: bytes):
+    buf = np.frombuffer(snapshot, dtype=np.uint8)
+    _check(ctx, lib.et_restore(ctx.handle, _p(buf), len(buf)))
 
