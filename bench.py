@@ -48,14 +48,17 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jittered", choices=["jittered", "small", "mixed"])
+    ap.add_argument("--workload", default="jittered", choices=["jittered", "small", "mixed", "uneven"])
+    ap.add_argument("--config", type=int, default=None, choices=[1, 2, 3, 4],
+                    help="the workload by number: 1 small, 2 jittered (default), 3 mixed, 4 uneven")
     ap.add_argument("--form", default="dense", choices=["dense", "sparse"])
     ap.add_argument("--layout", default="aosoa32", choices=["aos", "soa", "aosoa8", "aosoa16", "aosoa32",
                                                          "aosoa64", "aosoa128", "hotcold"])
     ap.add_argument("--driver", default="persistent", choices=["hostloop", "graph", "persistent", "hybrid"])
     ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
     ap.add_argument("--block-size", type=int, default=256)
-    ap.add_argument("--capacity-log2", type=int, default=22)
+    ap.add_argument("--capacity-log2", type=int, default=None,
+                    help="track slots per type: 2^N (default per workload: 16, 22, 24, 26)")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true")
@@ -64,7 +67,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--serving-events", type=int, default=200)
-    return ap.parse_args(argv)
+    a = ap.parse_args(argv)
+    if a.config is not None:
+        a.workload = {1: "small", 2: "jittered", 3: "mixed", 4: "uneven"}[a.config]
+    if a.capacity_log2 is None:
+        a.capacity_log2 = {"small": 16, "jittered": 22, "mixed": 24, "uneven": 26}[a.workload]
+    return a
 
 
 # ------------------------------------------------------------------ distributed plumbing
@@ -113,9 +121,13 @@ def make_workload(name: str, rank: int):
     elif name == "small":
         p = W.small_electrons()
         desc = "16 e- 1 GeV on +z, 50x(2.3 mm Pb + 5.7 mm lAr)"
-    else:
+    elif name == "mixed":
         p = W.mixed_primaries(10000, seed=W.PRIMARY_SEED + rank)
         desc = "10000 mixed e-/e+/gamma 0.1-100 GeV, 1 cm2 spot, 50x(2.3 mm Pb + 5.7 mm lAr)"
+    else:
+        p = W.uneven_events(256, 1000, seed=W.PRIMARY_SEED + rank)
+        desc = ("256 events of 1-1000 mixed e-/e+/gamma primaries (0.1-100 GeV), "
+                "50x(2.3 mm Pb + 5.7 mm lAr)")
     n_events = int(p["event"].max()) + 1
     return W.calorimeter(), p, n_events, desc
 
@@ -216,15 +228,15 @@ def committed_traffic(kernel_key: str):
 
 
 def run_config(et, geom, prim, n_events, args, form, layout, driver, steps, warmup, flush,
-               timing=True):
+               timing=True, reuse_slots=False):
     import torch
-    # the sparse form never reuses a slot: it needs room for every track of the run
+    # the sparse form without slot reuse needs room for every track of the run
     cap = args.capacity_log2 if form == "dense" else max(args.capacity_log2, 24)
     ctx = et.make_context(geom, max_events=n_events, capacity_log2=cap,
                           form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
                           layout=layout, driver=driver,
                           mode=et.MODE_STRICT if args.mode == "strict" else et.MODE_FAST,
-                          block_size=args.block_size, seed=1)
+                          block_size=args.block_size, seed=1, reuse_slots=reuse_slots)
     d_prim = torch.from_numpy(prim.view(np.uint8).copy()).cuda()
     n = len(prim)
     stream = torch.cuda.current_stream()
@@ -302,15 +314,21 @@ def serving_measure(geom, args):
     return out
 
 
-def cpu_baseline(geom, prim, n_events):
+def cpu_baseline(geom, prim, n_events, max_events=None):
+    """The oracle on the host cores: the whole workload, or its first max_events events."""
     import oracle
+    from paper_2302_08252_gb300 import workloads as W
+    what = "whole workload"
+    if max_events is not None and n_events > max_events:
+        prim = W.select_events(prim, list(range(max_events)))
+        what = f"first {max_events} of {n_events} events"
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     r = oracle.run(geom, prim, n_events=n_events, seed=1, nthreads=cores)
     dt = time.perf_counter() - t0
     steps = int(r["steps"].sum())
     return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"whole workload ({len(prim)} primaries, {steps} steps) on {cores} threads,"
+            "sample": f"{what} ({len(prim)} primaries, {steps} steps) on {cores} threads,"
                       f" {dt:.2f} s wall"}
 
 
@@ -322,7 +340,8 @@ def reference_arm(args, rank, world):
     import oracle
     from paper_2302_08252_gb300 import workloads as W
     geom, prim, n_events, desc = make_workload(args.workload, 0)
-    events = list(range(min(n_events, 100)))
+    # a bounded sample: about 10^7 track-steps per step on the host cores
+    events = list(range(min(n_events, 4 if args.workload == "uneven" else 100)))
     sample = W.select_events(prim, events)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
@@ -422,16 +441,21 @@ def ours_arm(args, rank, world, group):
                    "d2h_bytes_per_step": d2h}
     if rank == 0 and world == 1:
         if not args.no_plain:
+            # the large workloads create more tracks than a sparse buffer without reuse
+            # can hold: there the plain form reuses the slots of dead tracks
+            reuse = args.workload in ("mixed", "uneven")
             plain = run_config(et, geom, prim, n_events, args, "sparse", "aos", "hostloop",
-                               args.plain_steps, 1, flush, timing=False)
+                               args.plain_steps, 1, flush, timing=False, reuse_slots=reuse)
             pv = plain["steps"] / (sum(plain["ms"]) / 1e3)
             line["plain"] = {"value": pv, "unit": UNIT, "form": "sparse", "layout": "aos",
-                             "driver": "hostloop", "steps": args.plain_steps}
+                             "driver": "hostloop", "steps": args.plain_steps,
+                             "reuse_slots": reuse}
             line["tuned_vs_plain"] = value / pv
         if not args.no_serving:
             line["serving"] = serving_measure(geom, args)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events)
+            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events,
+                                                max_events=32 if args.workload == "uneven" else None)
     line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)
     if rank == 0:
         print(json.dumps(line), flush=True)
