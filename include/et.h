@@ -7,7 +7,7 @@
  * "dense double buffer" (two dense arrays, current and next, filled by
  * compaction, Sec. 2 / Fig. 1b) or in a "sparse single buffer" (one sparse
  * array plus two slot lists, Sec. 2 / Fig. 1a), in one of the layouts of
- * Sec. 4 (AoS, SoA, AoSoA-32, AoSoA-64), optionally instrumented to count
+ * Sec. 3-4 (AoS, SoA, AoSoA-N; plus a hot/cold split), optionally instrumented to count
  * per-field reads/writes and per-word accesses (Sec. 5).  The benchmark shape
  * (an electron gun into 50 absorber/gap layers, energy scored per layer) is
  * that of Sec. 4; the physics is a fixed toy EM model.
@@ -179,13 +179,21 @@ typedef struct {
   uint64_t secondaries;     /* secondaries created */
 } et_iter_stats;
 
-/* One transport iteration (always host-driven; stats may be NULL). */
+/*
+ * One transport iteration (Sec. 2): every active track takes one step; survivors and
+ * secondaries become the next iteration's tracks.  Host-driven whatever the driver: the
+ * per-type step kernels, then the end-of-iteration kernel.  out (may be NULL): tracks active in the next
+ * iteration, steps and secondaries of this one.  ET_ERR_CAPACITY when a track buffer or
+ * the iteration log overflows; ET_ERR_STATE before geometry and tables.
+ */
 et_status et_run_iteration(et_ctx* ctx, et_iter_stats* out);
 
 /*
- * Iterate until no track is left or max_iters more iterations ran, with the
- * configured driver (host loop, CUDA graph, persistent kernel).  Totals and
- * the number of iterations run are optional outputs.  The persistent driver
+ * Iterate (Sec. 2) until no track is left or max_iters more iterations ran, with
+ * the configured driver (host loop, CUDA graph, persistent kernel, hybrid).
+ * Totals and the number of iterations run are optional outputs.  Errors as for
+ * et_run_iteration, plus ET_ERR_TIMEOUT when a bounded wait of the persistent
+ * kernel's grid barrier ran out (the context then needs et_reset).  The persistent driver
  * issues one launch and one read-back (the launch records its starting
  * counters); the others read the counters back before they start.  Returns
  * after the stream has finished the run.
@@ -198,7 +206,14 @@ typedef struct {
   double injected, deposited_cont, below_cut, escaped, mass_created, mass_consumed;
 } et_ledger;
 
-/* Per-slab deposits (continuous + below-cut, FP64) and the ledger of one event. */
+/*
+ * The energy scored per layer (the benchmark's observable, paper Sec. 4) for one
+ * event: slab_dep[n_slabs] (host, may be NULL; n_slabs >= the geometry's) receives the
+ * per-slab deposits in MeV (continuous loss in the slab a step started in, plus
+ * below-cut remainders in the slab a track ended in; FP64 sums), out (may be NULL) the
+ * event's ledger.  Synchronises.  ET_ERR_INVALID for event >= max_events or a short
+ * buffer.
+ */
 et_status et_read_scoring(et_ctx* ctx, uint32_t event, double* slab_dep, size_t n_slabs,
                           et_ledger* out);
 
