@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import hashlib
+import re
 import os
 import shutil
 import subprocess
@@ -55,14 +56,22 @@ KERNEL_SOURCES = ("kernels_tu.cu", "kernels.cuh", "physics.cuh", "layout.cuh", "
                   "registry.h")
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and whitespace (what the compiler sees)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def kernel_fingerprint() -> str:
-    """Hash of the transport kernels' sources and flags: a profile taken on one build
-    stays valid while this is unchanged (host-side code may change)."""
+    """Hash of the transport kernels' code (comments and whitespace removed) and flags: a
+    profile taken on one build stays valid while this is unchanged (host-side code and
+    comments may change)."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(CSRC, name), "rb") as f:
+        with open(os.path.join(CSRC, name), encoding="utf-8") as f:
             h.update(name.encode())
-            h.update(f.read())
+            h.update(_code_only(f.read()).encode())
     flags = [f for f in COMMON if f not in (INC, CSRC)] + STRICT + FAST  # no machine paths
     h.update(" ".join(flags).encode())
     return h.hexdigest()

@@ -279,7 +279,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
 
 et_status et_destroy(et_ctx* c) {
   if (!c) return ET_ERR_INVALID;
-  if (c->stream || true) cudaStreamSynchronize(c->stream);
+  cudaStreamSynchronize(c->stream);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->graph) cudaGraphDestroy(c->graph);
   for (auto& p : c->evpool) {
@@ -720,14 +720,8 @@ et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* total
         if (s != ET_OK) return s;
         if (empty) break;
       }
-    } else {
-      if (c->cfg.driver == ET_DRIVER_GRAPH) {
-        s = launch_graph(c, (uint32_t)lim);
-      } else {  // persistent with max_iters == 0 does not get here
-        c->h_stop[0] = (uint32_t)lim;
-        CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_iter, c->h_stop, 4, cudaMemcpyHostToDevice, c->stream));
-        s = launch_persistent(c, 0u);
-      }
+    } else {  // the graph (the persistent and hybrid drivers returned above)
+      s = launch_graph(c, (uint32_t)lim);
       if (s != ET_OK) return s;
     }
   }

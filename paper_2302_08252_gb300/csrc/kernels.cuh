@@ -6,16 +6,18 @@
 //  dense double buffer: per type, track i of the current array is stepped and
 //    its survivor and secondaries are appended to the next array.  Slots are
 //    handed out by warp-aggregated allocation: one inclusive warp scan over
-//    per-lane counts packed 10 bits per type, then one atomicAdd per type per
-//    warp (ballot/popc style), so a warp's records land contiguously.
+//    per-lane counts packed 10 bits per type, then one 64-bit atomicAdd for the
+//    e- and gamma counters and one for e+ per warp, so a warp's records land
+//    contiguously.
 //  sparse single buffer: per type, one slot array plus two slot lists (current,
 //    next).  A survivor is updated in place (only the leaves the step changed)
 //    and its slot appended to the next list; secondaries get fresh slots from a
-//    high-water counter (never reused) or a free-slot stack (serving).
+//    high-water counter, or first from a ring of freed slots when slot reuse is on.
 //
-// Deposits: one FP64 atomicAdd per lane into score[event][slab]; the rarer
-// ledger terms (below cut, escaped, mass created/consumed) likewise.
-// Every kernel returns at once when the device status word is non-zero.
+// Deposits: one fire-and-forget FP64 reduction per lane into score[event][slab];
+// the rarer ledger terms (below cut, escaped, mass created/consumed) likewise.
+// The step kernels return at once when the device status word is non-zero; the
+// persistent kernel stops at the next iteration boundary.
 #pragma once
 
 #include <cuda/atomic>
