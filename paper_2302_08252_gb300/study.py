@@ -1,7 +1,7 @@
 """Layout and driver study (the comparison of the paper's Sec. 4 figure): runtime of one
 complete transport of a workload for every track-buffer form, layout and driver.
 
-    python -m paper_2302_08252_gb300.study [--workload jittered|mixed|uneven|small]
+    python -m paper_2302_08252_gb300.study [--workload jittered|mixed|uneven|uneven32|small]
         [--forms dense sparse] [--layouts aos soa aosoa32 aosoa64]
         [--drivers hostloop persistent graph] [--reps 3] [--out FILE]
 
@@ -31,6 +31,9 @@ def workload(name: str):
     if name == "uneven":
         p = W.uneven_events(256, 1000)
         return p, 256
+    if name == "uneven32":  # the first 32 of those events: a case small enough to profile
+        p = W.uneven_events(256, 1000)
+        return W.select_events(p, list(range(32))), 256
     raise ValueError(name)
 
 
@@ -45,7 +48,8 @@ def steps_of(geom, primaries, n_events, form, layout, driver, capacity_log2) -> 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="jittered", choices=["jittered", "small", "mixed", "uneven"])
+    ap.add_argument("--workload", default="jittered",
+                    choices=["jittered", "small", "mixed", "uneven", "uneven32"])
     ap.add_argument("--forms", nargs="+", default=["dense", "sparse"])
     ap.add_argument("--layouts", nargs="+", default=list(autotune.LAYOUTS))
     ap.add_argument("--drivers", nargs="+", default=["hostloop", "persistent"])
