@@ -314,10 +314,12 @@ def serving_measure(geom, args):
     return out
 
 
-def cpu_baseline(geom, prim, n_events, max_events=None):
-    """The oracle on the host cores: the whole workload, or its first max_events events."""
+def cpu_baseline(geom, prim, n_events, max_events=None, one_thread_events=50):
+    """The oracle on the host cores: the whole workload, or its first max_events events, on
+    every core; and, under "one_thread", its first one_thread_events events on one thread."""
     import oracle
     from paper_2302_08252_gb300 import workloads as W
+    full = prim
     what = "whole workload"
     if max_events is not None and n_events > max_events:
         prim = W.select_events(prim, list(range(max_events)))
@@ -327,9 +329,18 @@ def cpu_baseline(geom, prim, n_events, max_events=None):
     r = oracle.run(geom, prim, n_events=n_events, seed=1, nthreads=cores)
     dt = time.perf_counter() - t0
     steps = int(r["steps"].sum())
+    k = min(one_thread_events, n_events)
+    sample1 = W.select_events(full, list(range(k)))
+    t1 = time.perf_counter()
+    r1 = oracle.run(geom, sample1, n_events=n_events, seed=1, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    steps1 = int(r1["steps"].sum())
     return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{what} ({len(prim)} primaries, {steps} steps) on {cores} threads,"
-                      f" {dt:.2f} s wall"}
+                      f" {dt:.2f} s wall",
+            "one_thread": {"value": steps1 / dt1, "unit": UNIT, "cores": 1,
+                           "sample": f"first {k} events ({len(sample1)} primaries, {steps1}"
+                                     f" steps) on 1 thread, {dt1:.2f} s"}}
 
 
 # ------------------------------------------------------------------ arms
@@ -454,8 +465,10 @@ def ours_arm(args, rank, world, group):
         if not args.no_serving:
             line["serving"] = serving_measure(geom, args)
         if not args.no_cpu_baseline:
+            uneven = args.workload == "uneven"
             line["cpu_baseline"] = cpu_baseline(geom, prim, n_events,
-                                                max_events=32 if args.workload == "uneven" else None)
+                                                max_events=32 if uneven else None,
+                                                one_thread_events=1 if uneven else 50)
     line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -79,7 +79,7 @@ typedef struct {
   int32_t layout;           /* ET_LAYOUT_* */
   int32_t mode;             /* ET_MODE_*: strict = bit-exact toy model, fast = intrinsics + FMA */
   int32_t driver;           /* ET_DRIVER_*: how et_run_until_empty iterates */
-  int32_t block_size;       /* threads per block of the step kernels (64..1024, multiple of 32; 0 = 256) */
+  int32_t block_size;       /* threads per block of the step kernels (64..256, multiple of 32; 0 = 256) */
   uint64_t seed;            /* physics seed: Philox key word 0 is its low 32 bits */
   uint32_t max_events;      /* events are numbered 0..max_events-1 */
   uint32_t max_iters;       /* length of the per-iteration count log */
@@ -97,6 +97,14 @@ typedef struct {
   int32_t reuse_slots;      /* sparse form: 1 = slots of dead tracks are reused (from the next
                                iteration on); 0 = never reused (the plain single buffer) */
   uint32_t hybrid_tracks;   /* ET_DRIVER_HYBRID: the switch-over population (0 = 2^21) */
+  int32_t split_interactions; /* 1: split step kernels (host-loop, graph and the graph phase
+                               of hybrid): per type, a transport pass appends the steps that
+                               end in a discrete interaction to one global queue per process,
+                               then an interaction pass runs each queue with process-uniform
+                               warps -- the divergent code paths of Sec. 1 sorted out of the
+                               warps.  Same histories as the fused step.  Needs 96 bytes x
+                               2^capacity_log2 per process queue (5 queues); not with
+                               ET_DRIVER_PERSISTENT or instrument (ET_ERR_INVALID). */
 } et_config;
 
 /* Create a context (allocates the track buffers).  *out is NULL on failure. */

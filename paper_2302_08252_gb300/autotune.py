@@ -39,14 +39,14 @@ def sample_events(primaries: np.ndarray, n_events: int, seed: int = 7) -> np.nda
 
 
 def time_config(geom, primaries, n_events, form, layout, block, driver, reps=3,
-                capacity_log2=22) -> float:
-    """Best-of-reps seconds for one complete run (GPU)."""
+                capacity_log2=22, **ctx_kw) -> float:
+    """Best-of-reps seconds for one complete run (GPU); ctx_kw: further context options."""
     import torch
 
     from . import et
     ctx = et.make_context(geom, max_events=n_events, capacity_log2=capacity_log2,
                           form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
-                          layout=layout, driver=driver, block_size=block)
+                          layout=layout, driver=driver, block_size=block, **ctx_kw)
     d = torch.from_numpy(primaries.view(np.uint8).copy()).cuda()
     best = float("inf")
     for r in range(reps + 1):

@@ -68,6 +68,10 @@ enum : uint32_t {
 // (photon steps make electrons, electron steps make photons) with one atomic.
 __host__ __device__ constexpr int cw(int type) { return type == EM ? 0 : (type == GAM ? 1 : 2); }
 
+// Process queues of the split step kernels: the interactions of one iteration, sorted by
+// process (e- bremsstrahlung; e+ bremsstrahlung; photon Compton, pair, photoelectric).
+enum { IQ_BREM_EM = 0, IQ_BREM_EP = 1, IQ_COMPTON = 2, IQ_PAIR = 3, IQ_PHOT = 4, N_IQ = 5 };
+
 // ---- device control block (one per context) ----
 struct alignas(16) DevCtl {
   uint32_t cnt[3][4];          // tracks per type (word cw(t)); row it%3 current, (it+1)%3 next
@@ -95,6 +99,9 @@ struct alignas(16) DevCtl {
   uint32_t grab[4];  // persistent driver: dynamic chunk counter of iteration it (row it % 3)
   uint32_t run_iter0;
   unsigned long long run_steps0[NTYPES], run_sec0[NTYPES];
+  // split step kernels: entries in each process queue in this iteration (IQ_*); zeroed at
+  // the iteration's end
+  uint32_t iq_n[8];
 };
 
 // Iteration boundary bookkeeping of the slot-reuse rings (one thread, all other
@@ -150,6 +157,9 @@ struct Args {
   uint32_t done_cap;
   // sparse form with slot reuse: ring of freed slots per type (NULL: slots never reused)
   uint32_t* free_ring[NTYPES];  // [cap] each
+  // split step kernels: one global interaction queue per process (IQ_*), field-major
+  // records of QW words, [QW][cap] each (NULL: the split form is off)
+  uint32_t* iq[N_IQ];
 };
 
 constexpr int MAX_SLABS = 128;

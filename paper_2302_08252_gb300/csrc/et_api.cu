@@ -9,6 +9,7 @@
 // trip is needed between iterations except in the host-loop driver, which
 // mirrors the plain AdePT loop (launch per type, read counts back).
 #define ET_HOST_TU
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -56,8 +57,11 @@ struct et_ctx {
   bool h_stage_pending = false;
   int block = 256;
   int grid_fixed[3] = {0, 0, 0};  // step kernels in the graph driver (grid-stride)
+  int grid_tr[3] = {0, 0, 0}, grid_ia[3] = {0, 0, 0};  // split form: transport, interaction
   int grid_persistent = 0;
-  size_t smem_g = 0, smem_e = 0, smem_all = 0;
+  size_t smem_all = 0, smem_tab = 0;
+  size_t smem_step[3] = {0, 0, 0};  // per-type step kernels: the e+- kernels queue nothing
+  bool split = false;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   bool timing = false;
@@ -200,7 +204,9 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
       (k.layout == LAYOUT_AOSOA128 && k.capacity_log2 < 7) ||
       k.driver > 3 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
       k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) ||
-      ((k.alloc == nullptr) != (k.free == nullptr)))
+      ((k.alloc == nullptr) != (k.free == nullptr)) ||
+      (k.split_interactions != 0 && k.split_interactions != 1) ||
+      (k.split_interactions && (k.driver == ET_DRIVER_PERSISTENT || k.instrument)))
     return ET_ERR_INVALID;
   et_ctx* c = new et_ctx();
   c->cfg = k;
@@ -208,6 +214,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   c->cap = 1u << k.capacity_log2;
   c->dense = k.form == ET_FORM_DENSE;
   c->block = k.block_size;
+  c->split = k.split_interactions != 0;
   *out = c;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -265,6 +272,12 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
     for (int t = 0; t < 3; ++t) {
       a.free_ring[t] = (uint32_t*)dalloc(c, (size_t)c->cap * 4u);
       if (!a.free_ring[t]) return fail(c, ET_ERR_NOMEM, "free-slot ring");
+    }
+  }
+  if (c->split) {
+    for (int q = 0; q < N_IQ; ++q) {
+      a.iq[q] = (uint32_t*)dalloc(c, (size_t)c->cap * QW * 4u);
+      if (!a.iq[q]) return fail(c, ET_ERR_NOMEM, "interaction queue");
     }
   }
   a.seed_lo = (uint32_t)k.seed;
@@ -405,17 +418,33 @@ et_status et_load_tables(et_ctx* c, uint32_t n_materials, uint32_t n_nodes, floa
   a.inv_dlog = inv_dlog;
   // dynamic shared memory: tables, then one interaction queue per warp
   c->smem_all = tables_bytes_aligned((int)n_materials) + (size_t)(c->block / 32) * queue_bytes_per_warp();
-  c->smem_g = c->smem_all;
-  c->smem_e = c->smem_all;
+  // only photon interactions are parked in the warp queues: the e+- step kernels need the
+  // tables alone, which leaves room for more blocks per SM
+  c->smem_tab = tables_bytes_aligned((int)n_materials);
+  c->smem_step[EM] = c->smem_step[EP] = c->smem_tab;
+  c->smem_step[GAM] = c->smem_all;
   const void* pf = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
   CUDA_TRY(c, cudaFuncSetAttribute(pf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_all));
   // grids: grid-stride kernels sized to fill the machine
   int occ = 0;
   for (int t = 0; t < 3; ++t) {
     const void* fn = c->ks.step[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0][t];
-    CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_all));
-    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->block, c->smem_all));
+    CUDA_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_step[t]));
+    CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, c->block, c->smem_step[t]));
     c->grid_fixed[t] = (occ > 0 ? occ : 1) * c->num_sms;
+  }
+  if (c->split) {
+    // the transport pass stages the tables only; the interaction pass needs no shared memory
+    const int dn = c->dense ? 1 : 0;
+    for (int t = 0; t < 3; ++t) {
+      const void* ft = c->ks.transport[dn][t];
+      const void* fi = c->ks.interact[dn][t];
+      CUDA_TRY(c, cudaFuncSetAttribute(ft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem_tab));
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ft, c->block, c->smem_tab));
+      c->grid_tr[t] = (occ > 0 ? occ : 1) * c->num_sms;
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fi, c->block, 0));
+      c->grid_ia[t] = (occ > 0 ? occ : 1) * c->num_sms;
+    }
   }
   CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pf, c->block, c->smem_all));
   if (occ < 1) return fail(c, ET_ERR_CUDA, "persistent kernel does not fit on an SM");
@@ -491,17 +520,31 @@ et_status et_inject_device(et_ctx* c, const et_primary* p, size_t n) {
   return launch(c, c->ks.inject[c->dense ? 1 : 0], (int)((n + 255) / 256), 256, 0, params);
 }
 
-// Launch the three step kernels of one iteration; counts from the last read-back.
-static et_status launch_step_kernels(et_ctx* c, const uint32_t n[3], bool fixed_grid) {
+// The step of type t: one step kernel, or (split form) the transport pass then the
+// interaction pass.  grid: the step kernel's grid, 0 = the fixed (grid-stride) grids.
+static et_status launch_type_step(et_ctx* c, int t, int grid) {
   void* params[] = {(void*)&c->args};
   const int instr = c->cfg.instrument ? 1 : 0, dn = c->dense ? 1 : 0;
+  if (!c->split)
+    return launch(c, c->ks.step[instr][dn][t], grid ? grid : c->grid_fixed[t], c->block,
+                  c->smem_step[t], params);
+  et_status s = launch(c, c->ks.transport[dn][t], grid ? std::min(grid, c->grid_tr[t]) : c->grid_tr[t],
+                       c->block, c->smem_tab, params);
+  if (s != ET_OK) return s;
+  // at most as many interactions as tracks
+  return launch(c, c->ks.interact[dn][t], grid ? std::min(grid, c->grid_ia[t]) : c->grid_ia[t],
+                c->block, 0, params);
+}
+
+// Launch the step kernels of one iteration; counts from the last read-back.
+static et_status launch_step_kernels(et_ctx* c, const uint32_t n[3], bool fixed_grid) {
   for (int t = 0; t < 3; ++t) {
     if (!fixed_grid && n[t] == 0) continue;
     int grid = fixed_grid ? c->grid_fixed[t] : (int)((n[t] + c->block - 1) / c->block);
     if (grid > c->grid_fixed[t]) grid = c->grid_fixed[t];
     if (grid < 1) grid = 1;
     EventPair* ev = fixed_grid ? nullptr : timing_begin(c);
-    et_status s = launch(c, c->ks.step[instr][dn][t], grid, c->block, c->smem_all, params);
+    et_status s = launch_type_step(c, t, fixed_grid ? 0 : grid);
     timing_end(c, ev);
     if (s != ET_OK) return s;
   }
@@ -597,11 +640,9 @@ static et_status build_graph(et_ctx* c) {
                        cudaStreamWaitEvent(br[0], ev[0], 0) != cudaSuccess ||
                        cudaStreamWaitEvent(br[1], ev[0], 0) != cudaSuccess))
       s = fail(c, ET_ERR_CUDA, "graph fork");
-    const int instr = c->cfg.instrument ? 1 : 0, dn = c->dense ? 1 : 0;
-    void* params[] = {(void*)&c->args};
     for (int t = 0; t < 3 && s == ET_OK; ++t) {
       c->stream = t == 0 ? cs : br[t - 1];
-      s = launch(c, c->ks.step[instr][dn][t], c->grid_fixed[t], c->block, c->smem_all, params);
+      s = launch_type_step(c, t, 0);
     }
     c->stream = cs;
     if (s == ET_OK && (cudaEventRecord(ev[1], br[0]) != cudaSuccess ||

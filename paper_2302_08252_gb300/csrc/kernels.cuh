@@ -299,59 +299,63 @@ struct WarpQueue {
   uint32_t head, count;  // warp-uniform
 };
 
-__device__ __forceinline__ void q_put(uint32_t* q, uint32_t s, const Trk& t, const Ctx& cx,
-                                      uint32_t slot) {
-  q[0 * QCAP + s] = __float_as_uint(t.x);
-  q[1 * QCAP + s] = __float_as_uint(t.y);
-  q[2 * QCAP + s] = __float_as_uint(t.z);
-  q[3 * QCAP + s] = __float_as_uint(t.dx);
-  q[4 * QCAP + s] = __float_as_uint(t.dy);
-  q[5 * QCAP + s] = __float_as_uint(t.dz);
-  q[6 * QCAP + s] = __float_as_uint(t.e);
-  q[7 * QCAP + s] = __float_as_uint(t.nia);
-  q[8 * QCAP + s] = (uint32_t)t.id;
-  q[9 * QCAP + s] = (uint32_t)(t.id >> 32);
-  q[10 * QCAP + s] = t.event;
-  q[11 * QCAP + s] = t.step;
-  q[12 * QCAP + s] = (uint32_t)t.slab;
-  q[13 * QCAP + s] = __float_as_uint(t.time);
-  q[14 * QCAP + s] = __float_as_uint(t.len);
-  q[15 * QCAP + s] = t.flags;
-  q[16 * QCAP + s] = __float_as_uint(cx.E);
-  q[17 * QCAP + s] = __float_as_uint(cx.sig);
-  q[18 * QCAP + s] = __float_as_uint(cx.sc);
-  q[19 * QCAP + s] = __float_as_uint(cx.sp);
-  q[20 * QCAP + s] = __float_as_uint(cx.u1);
-  q[21 * QCAP + s] = __float_as_uint(cx.u2);
-  q[22 * QCAP + s] = __float_as_uint(cx.u3);
-  q[23 * QCAP + s] = slot;
+// One queue record: word w of entry s at q[w * ld + s] (ld = QCAP, 32-bit indexing, in
+// shared memory; the queue capacity, 64-bit indexing, in global memory).
+template <typename LD>
+__device__ __forceinline__ void q_put(uint32_t* q, LD ld, uint32_t s, const Trk& t,
+                                      const Ctx& cx, uint32_t slot) {
+  q[0 * ld + s] = __float_as_uint(t.x);
+  q[1 * ld + s] = __float_as_uint(t.y);
+  q[2 * ld + s] = __float_as_uint(t.z);
+  q[3 * ld + s] = __float_as_uint(t.dx);
+  q[4 * ld + s] = __float_as_uint(t.dy);
+  q[5 * ld + s] = __float_as_uint(t.dz);
+  q[6 * ld + s] = __float_as_uint(t.e);
+  q[7 * ld + s] = __float_as_uint(t.nia);
+  q[8 * ld + s] = (uint32_t)t.id;
+  q[9 * ld + s] = (uint32_t)(t.id >> 32);
+  q[10 * ld + s] = t.event;
+  q[11 * ld + s] = t.step;
+  q[12 * ld + s] = (uint32_t)t.slab;
+  q[13 * ld + s] = __float_as_uint(t.time);
+  q[14 * ld + s] = __float_as_uint(t.len);
+  q[15 * ld + s] = t.flags;
+  q[16 * ld + s] = __float_as_uint(cx.E);
+  q[17 * ld + s] = __float_as_uint(cx.sig);
+  q[18 * ld + s] = __float_as_uint(cx.sc);
+  q[19 * ld + s] = __float_as_uint(cx.sp);
+  q[20 * ld + s] = __float_as_uint(cx.u1);
+  q[21 * ld + s] = __float_as_uint(cx.u2);
+  q[22 * ld + s] = __float_as_uint(cx.u3);
+  q[23 * ld + s] = slot;
 }
 
-__device__ __forceinline__ void q_get(const uint32_t* q, uint32_t s, Trk& t, Ctx& cx,
+template <typename LD>
+__device__ __forceinline__ void q_get(const uint32_t* q, LD ld, uint32_t s, Trk& t, Ctx& cx,
                                       uint32_t& slot) {
-  t.x = __uint_as_float(q[0 * QCAP + s]);
-  t.y = __uint_as_float(q[1 * QCAP + s]);
-  t.z = __uint_as_float(q[2 * QCAP + s]);
-  t.dx = __uint_as_float(q[3 * QCAP + s]);
-  t.dy = __uint_as_float(q[4 * QCAP + s]);
-  t.dz = __uint_as_float(q[5 * QCAP + s]);
-  t.e = __uint_as_float(q[6 * QCAP + s]);
-  t.nia = __uint_as_float(q[7 * QCAP + s]);
-  t.id = (uint64_t)q[8 * QCAP + s] | ((uint64_t)q[9 * QCAP + s] << 32);
-  t.event = q[10 * QCAP + s];
-  t.step = q[11 * QCAP + s];
-  t.slab = (int32_t)q[12 * QCAP + s];
-  t.time = __uint_as_float(q[13 * QCAP + s]);
-  t.len = __uint_as_float(q[14 * QCAP + s]);
-  t.flags = q[15 * QCAP + s];
-  cx.E = __uint_as_float(q[16 * QCAP + s]);
-  cx.sig = __uint_as_float(q[17 * QCAP + s]);
-  cx.sc = __uint_as_float(q[18 * QCAP + s]);
-  cx.sp = __uint_as_float(q[19 * QCAP + s]);
-  cx.u1 = __uint_as_float(q[20 * QCAP + s]);
-  cx.u2 = __uint_as_float(q[21 * QCAP + s]);
-  cx.u3 = __uint_as_float(q[22 * QCAP + s]);
-  slot = q[23 * QCAP + s];
+  t.x = __uint_as_float(q[0 * ld + s]);
+  t.y = __uint_as_float(q[1 * ld + s]);
+  t.z = __uint_as_float(q[2 * ld + s]);
+  t.dx = __uint_as_float(q[3 * ld + s]);
+  t.dy = __uint_as_float(q[4 * ld + s]);
+  t.dz = __uint_as_float(q[5 * ld + s]);
+  t.e = __uint_as_float(q[6 * ld + s]);
+  t.nia = __uint_as_float(q[7 * ld + s]);
+  t.id = (uint64_t)q[8 * ld + s] | ((uint64_t)q[9 * ld + s] << 32);
+  t.event = q[10 * ld + s];
+  t.step = q[11 * ld + s];
+  t.slab = (int32_t)q[12 * ld + s];
+  t.time = __uint_as_float(q[13 * ld + s]);
+  t.len = __uint_as_float(q[14 * ld + s]);
+  t.flags = q[15 * ld + s];
+  cx.E = __uint_as_float(q[16 * ld + s]);
+  cx.sig = __uint_as_float(q[17 * ld + s]);
+  cx.sc = __uint_as_float(q[18 * ld + s]);
+  cx.sp = __uint_as_float(q[19 * ld + s]);
+  cx.u1 = __uint_as_float(q[20 * ld + s]);
+  cx.u2 = __uint_as_float(q[21 * ld + s]);
+  cx.u3 = __uint_as_float(q[22 * ld + s]);
+  slot = q[23 * ld + s];
 }
 
 // Everything after the physics of a finished step, for the lanes with act == true:
@@ -455,15 +459,20 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
 }
 
 // One warp transports up to 32 tracks of one type (lanes with valid == false idle).
-// With `batch` set, lanes whose step ends in a discrete interaction go into the warp's
-// queue, which is drained 32 entries at a time, or completely when `drain_all` is set
-// (the warp's last chunk of this type); a call with no valid lane only drains.
-// Without `batch` (iterations too small to fill a queue) the interactions run in place
-// and the whole chunk is finished in one pass: one slot reservation instead of two.
+// With `batch` set, lanes whose photon step ends in a discrete interaction go into the
+// warp's queue, which is drained 32 entries at a time, or completely when `drain_all` is
+// set (the warp's last chunk of this type); a call with no valid lane only drains.
+// Without `batch` (iterations too small to fill a queue), and for e+- at any size, the
+// interactions run in place and the whole chunk is finished in one pass: one slot
+// reservation instead of two.  Only photons are queued: the Compton sampler is long and
+// its rejection loop divergent, while a bremsstrahlung emission is short enough that
+// parking it costs more than the idle lanes it saves (measured: 3 % on the persistent
+// kernel, 5 % on the per-type kernels of the batched events).
 template <int MODE, int L, bool INSTR, bool DENSE>
 __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, const int type,
                                              uint32_t it, uint32_t i, bool valid, uint32_t lane,
                                              WarpQueue& wq, bool batch, bool drain_all, Tally& tl) {
+  batch = batch && type == GAM;
   const uint32_t hc = it & 1u;
   Trk t;
   StepOut o;
@@ -485,7 +494,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     const uint32_t mask = __ballot_sync(FULL, inter);
     if (inter) {
       const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
-      q_put(wq.q, pos, t, cx, slot);
+      q_put(wq.q, QCAP, pos, t, cx, slot);
     }
     wq.count += (uint32_t)__popc(mask);
     __syncwarp();
@@ -501,7 +510,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
       n = wq.count >= 32u ? 32u : wq.count;  // the n oldest queued entries, one per lane
       act = lane < n;
       do_int = act;
-      if (act) q_get(wq.q, (wq.head + lane) % QCAP, t, cx, s2);
+      if (act) q_get(wq.q, QCAP, (wq.head + lane) % QCAP, t, cx, s2);
     }
     if (do_int) interact<MODE>(type, t, cx, a.seed_lo, o);
     if (!once) __syncwarp();  // entries consumed before their ring slots are reused
@@ -558,6 +567,136 @@ __global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_step(const __grid_consta
   tally_flush(a, tl, lane);
 }
 
+// ---- split step kernels: a transport pass, then per-process interaction passes ----
+// The transport kernel of a type runs the transport half of the step for every track of
+// the type.  A step that ends without a discrete interaction is finished in place; the
+// others are appended, with their interaction context and slot, to the global queue of
+// their process (one warp-aggregated reservation per queue, field-major records).  The
+// interaction kernel of the type then runs its queues chunk by chunk, so that every warp
+// executes a single process, and finishes those steps.  The histories are those of the
+// fused step: the same functions run on the same values, only in two launches.
+
+// The process an interacting photon will take (the branch `interact` takes on the same
+// values); it only sorts the queues, `interact` decides again.
+__device__ __forceinline__ int photon_queue(const Ctx& cx) {
+  const float r = cx.u1 * cx.sig;
+  if (r < cx.sc) return IQ_COMPTON;
+  if (r < cx.sc + cx.sp && cx.E > TWO_MC2) return IQ_PAIR;
+  return IQ_PHOT;
+}
+
+template <int TYPE>
+struct TypeQueues {
+  static constexpr int first = TYPE == EM ? IQ_BREM_EM : (TYPE == EP ? IQ_BREM_EP : IQ_COMPTON);
+  static constexpr int count = TYPE == GAM ? 3 : 1;
+};
+
+template <int TYPE>
+__device__ __forceinline__ uint32_t* queue_of(const Args& a, int k) {
+  if constexpr (TYPE == GAM) return sel3(k, a.iq[IQ_COMPTON], a.iq[IQ_PAIR], a.iq[IQ_PHOT]);
+  else return a.iq[TypeQueues<TYPE>::first];
+}
+
+template <int TYPE, int MODE, int L, bool DENSE>
+__global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_transport(const __grid_constant__ Args a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Tabs tb = stage_tables<TYPE == GAM, TYPE != GAM>(smem, a);
+  DevCtl* ctl = a.ctl;
+  if (ctl->status != 0) return;
+  const uint32_t it = ctl->iter;
+  const uint32_t hc = it & 1u;
+  uint32_t n = ctl->cnt[it % 3][cw(TYPE)];
+  n = n < a.cap ? n : a.cap;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;  // block-first, as k_step
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t chunks = (n + 31u) / 32u;
+  using Q = TypeQueues<TYPE>;
+  Tally tl;
+  tally_reset(tl);
+  for (uint32_t ch = gw; ch < chunks; ch += nw) {
+    const uint32_t i = ch * 32u + lane;
+    const bool valid = i < n;
+    Trk t;
+    StepOut o;
+    Ctx cx;
+    uint32_t slot = 0;
+    bool inter = false;
+    if (valid) {
+      if constexpr (DENSE) {
+        slot = i;
+        t = view_of<L, false>(a, TYPE, (int)hc).load(slot);
+      } else {
+        slot = __ldcg(idx_of(a, TYPE, (int)hc) + i);
+        t = view_of<L, false>(a, TYPE, 0).load(slot);
+      }
+      inter = transport<MODE>(TYPE, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
+    }
+    finish<L, false, DENSE>(a, TYPE, it, lane, valid && !inter, t, o, slot, tl);
+    // queue positions: one inclusive scan of per-queue counts packed 10 bits per queue,
+    // then one atomicAdd per non-empty queue
+    const int k = (TYPE == GAM && inter) ? photon_queue(cx) - IQ_COMPTON : 0;
+    const uint32_t packed = inter ? 1u << (10 * k) : 0u;
+    const uint32_t incl = warp_incl_scan(packed, lane);
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    uint32_t b[3] = {0u, 0u, 0u};
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < Q::count; ++j) {
+        const uint32_t m = (total >> (10 * j)) & 1023u;
+        if (m) b[j] = atomicAdd(&ctl->iq_n[Q::first + j], m);
+      }
+    }
+    uint32_t base = 0;
+#pragma unroll
+    for (int j = 0; j < Q::count; ++j) {
+      const uint32_t bj = __shfl_sync(FULL, b[j], 0);
+      if (j == k) base = bj;
+    }
+    if (inter) {
+      const uint32_t at = base + (((incl - packed) >> (10 * k)) & 1023u);
+      if (at < a.cap) q_put(queue_of<TYPE>(a, k), (size_t)a.cap, at, t, cx, slot);
+      else atomicOr(&ctl->status, ST_CAPACITY);
+    }
+  }
+  tally_flush(a, tl, lane);
+}
+
+template <int TYPE, int MODE, int L, bool DENSE>
+__global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_interact(const __grid_constant__ Args a) {
+  const DevCtl* ctl = a.ctl;
+  if (ctl->status != 0) return;
+  const uint32_t it = ctl->iter;
+  using Q = TypeQueues<TYPE>;
+  uint32_t m[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < Q::count; ++j) m[j] = min(ctl->iq_n[Q::first + j], a.cap);
+  // chunk index space [queue 0 chunks][queue 1 chunks][queue 2 chunks]
+  const uint32_t w0 = (m[0] + 31u) / 32u, w1 = (m[1] + 31u) / 32u, w2 = (m[2] + 31u) / 32u;
+  const uint32_t wt = w0 + w1 + w2;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  Tally tl;
+  tally_reset(tl);
+  for (uint32_t ch = gw; ch < wt; ch += nw) {
+    const int k = ch < w0 ? 0 : (ch < w0 + w1 ? 1 : 2);
+    const uint32_t first = k == 0 ? 0u : (k == 1 ? w0 : w0 + w1);
+    const uint32_t p = (ch - first) * 32u + lane;
+    const bool act = p < sel3(k, m[0], m[1], m[2]);
+    Trk t;
+    StepOut o;
+    Ctx cx;
+    uint32_t slot = 0;
+    if (act) {
+      q_get(queue_of<TYPE>(a, k), (size_t)a.cap, p, t, cx, slot);
+      interact<MODE>(TYPE, t, cx, a.seed_lo, o);
+    }
+    finish<L, false, DENSE>(a, TYPE, it, lane, act, t, o, slot, tl);
+  }
+  tally_flush(a, tl, lane);
+}
+
 #ifdef ET_HOST_TU
 // ---- end of iteration (one thread): log counts, recycle the count slot, advance ----
 __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditionalHandle cond,
@@ -575,6 +714,7 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
   if (it >= a.max_iters && !a.iter_log_wrap) c->status |= ST_ITER_LOG_FULL;
   free_ring_boundary(c);
   for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
+  for (int q = 0; q < N_IQ; ++q) c->iq_n[q] = 0;  // split form: the queues are consumed
   c->iter = it + 1;
   const uint32_t left = c->cnt[nxt][0] + c->cnt[nxt][1] + c->cnt[nxt][2];
   const bool stop = left == 0 || c->status != 0 || it + 1 >= c->stop_iter ||

@@ -30,6 +30,17 @@ static void fill(KernelSet* ks) {
   ks->persistent[INSTR][0] = (const void*)k_persistent<M, L, INSTR, false>;
 }
 
+template <bool DENSE>
+static void fill_split(KernelSet* ks) {
+  constexpr int M = ET_MODE, L = ET_LAYOUT, D = DENSE ? 1 : 0;
+  ks->transport[D][EM] = (const void*)k_transport<EM, M, L, DENSE>;
+  ks->transport[D][EP] = (const void*)k_transport<EP, M, L, DENSE>;
+  ks->transport[D][GAM] = (const void*)k_transport<GAM, M, L, DENSE>;
+  ks->interact[D][EM] = (const void*)k_interact<EM, M, L, DENSE>;
+  ks->interact[D][EP] = (const void*)k_interact<EP, M, L, DENSE>;
+  ks->interact[D][GAM] = (const void*)k_interact<GAM, M, L, DENSE>;
+}
+
 }  // namespace et
 
 extern "C" void ET_CAT(ET_MODE, ET_LAYOUT)(et::KernelSet* ks) {
@@ -39,4 +50,6 @@ extern "C" void ET_CAT(ET_MODE, ET_LAYOUT)(et::KernelSet* ks) {
 #endif
   ks->inject[1] = (const void*)et::k_inject<ET_LAYOUT, true>;
   ks->inject[0] = (const void*)et::k_inject<ET_LAYOUT, false>;
+  et::fill_split<true>(ks);
+  et::fill_split<false>(ks);
 }

@@ -52,7 +52,8 @@ class et_config(C.Structure):
                 ("instrument", C.c_int32), ("id_log", C.c_int32),
                 ("id_log_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("serving", C.c_int32), ("reuse_slots", C.c_int32), ("hybrid_tracks", C.c_uint32)]
+                ("serving", C.c_int32), ("reuse_slots", C.c_int32), ("hybrid_tracks", C.c_uint32),
+                ("split_interactions", C.c_int32)]
 
 
 class et_iter_stats(C.Structure):
@@ -168,7 +169,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
               driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
               instrument=False, id_log=False, id_log_capacity=0, stream=None,
               use_torch_allocator=True, serving=False, reuse_slots=False,
-              allocator=None, hybrid_tracks=0) -> Context:
+              allocator=None, hybrid_tracks=0, split=False) -> Context:
     """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
     torch's current stream.  allocator: optional (alloc(nbytes, stream) -> int address,
     free(address)) pair of Python callables for the library's device buffers; default
@@ -199,6 +200,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
     cfg.serving = int(bool(serving))
     cfg.reuse_slots = int(bool(reuse_slots))
     cfg.hybrid_tracks = int(hybrid_tracks)
+    cfg.split_interactions = int(bool(split))
     cbs = None
     if allocator is not None:
         fa, ff = allocator

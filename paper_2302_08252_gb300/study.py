@@ -3,11 +3,13 @@ complete transport of a workload for every track-buffer form, layout and driver.
 
     python -m paper_2302_08252_gb300.study [--workload jittered|mixed|uneven|uneven32|small]
         [--forms dense sparse] [--layouts aos soa aosoa32 aosoa64]
-        [--drivers hostloop persistent graph] [--reps 3] [--out FILE]
+        [--drivers hostloop persistent graph] [--split 0 1] [--reps 3] [--out FILE]
 
 Prints one JSON object per candidate (track-steps/s, best-of-reps seconds) and writes
-the list to --out.  Every candidate computes the same histories in strict mode, so only
-the time differs.  GPU required.
+the list to --out.  `--split 1` times the split step kernels (transport pass, then
+per-process interaction passes) of the host-loop, graph and hybrid drivers.  Every
+candidate computes the same histories in strict mode, so only the time differs.  GPU
+required.
 """
 from __future__ import annotations
 
@@ -37,11 +39,11 @@ def workload(name: str):
     raise ValueError(name)
 
 
-def steps_of(geom, primaries, n_events, form, layout, driver, capacity_log2) -> int:
+def steps_of(geom, primaries, n_events, form, layout, driver, capacity_log2, **ctx_kw) -> int:
     from . import et
     ctx = et.make_context(geom, max_events=n_events, capacity_log2=capacity_log2,
                           form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
-                          layout=layout, driver=driver)
+                          layout=layout, driver=driver, **ctx_kw)
     et.et_inject(ctx, primaries)
     return int(et.et_run_until_empty(ctx)["steps"])
 
@@ -53,6 +55,7 @@ def main(argv=None):
     ap.add_argument("--forms", nargs="+", default=["dense", "sparse"])
     ap.add_argument("--layouts", nargs="+", default=list(autotune.LAYOUTS))
     ap.add_argument("--drivers", nargs="+", default=["hostloop", "persistent"])
+    ap.add_argument("--split", nargs="+", type=int, default=[0], choices=[0, 1])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--dense-capacity-log2", type=int, default=22)
     ap.add_argument("--sparse-capacity-log2", type=int, default=24)
@@ -67,15 +70,19 @@ def main(argv=None):
         cap = a.dense_capacity_log2 if form == "dense" else a.sparse_capacity_log2
         for layout in a.layouts:
             for driver in a.drivers:
-                if steps is None:
-                    steps = steps_of(geom, prim, n_events, form, layout, driver, cap)
-                t = autotune.time_config(geom, prim, n_events, form, layout, a.block_size,
-                                         driver, reps=a.reps, capacity_log2=cap)
-                r = {"workload": a.workload, "form": form, "layout": layout, "driver": driver,
-                     "block_size": a.block_size, "seconds": t, "steps": steps,
-                     "track_steps_per_s": steps / t}
-                rows.append(r)
-                print(json.dumps(r), flush=True)
+                for split in a.split:
+                    if split and driver == "persistent":
+                        continue  # no split form of the persistent kernel
+                    kw = {"split": True} if split else {}
+                    if steps is None:
+                        steps = steps_of(geom, prim, n_events, form, layout, driver, cap, **kw)
+                    t = autotune.time_config(geom, prim, n_events, form, layout, a.block_size,
+                                             driver, reps=a.reps, capacity_log2=cap, **kw)
+                    r = {"workload": a.workload, "form": form, "layout": layout,
+                         "driver": driver, "split": bool(split), "block_size": a.block_size,
+                         "seconds": t, "steps": steps, "track_steps_per_s": steps / t}
+                    rows.append(r)
+                    print(json.dumps(r), flush=True)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rows, f, indent=1)
