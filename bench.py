@@ -54,7 +54,9 @@ def parse_args(argv=None):
     ap.add_argument("--form", default="dense", choices=["dense", "sparse"])
     ap.add_argument("--layout", default="aosoa32", choices=["aos", "soa", "aosoa8", "aosoa16", "aosoa32",
                                                          "aosoa64", "aosoa128", "hotcold"])
-    ap.add_argument("--driver", default="persistent", choices=["hostloop", "graph", "persistent", "hybrid"])
+    ap.add_argument("--driver", default=None, choices=["hostloop", "graph", "persistent", "hybrid"],
+                    help="default per workload: persistent for the single showers, hybrid for"
+                         " the mixed primaries and the batched events (the fastest measured)")
     ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--capacity-log2", type=int, default=None,
@@ -70,6 +72,9 @@ def parse_args(argv=None):
     a = ap.parse_args(argv)
     if a.config is not None:
         a.workload = {1: "small", 2: "jittered", 3: "mixed", 4: "uneven"}[a.config]
+    if a.driver is None:
+        a.driver = {"small": "persistent", "jittered": "persistent", "mixed": "hybrid",
+                    "uneven": "hybrid"}[a.workload]
     if a.capacity_log2 is None:
         a.capacity_log2 = {"small": 16, "jittered": 22, "mixed": 24, "uneven": 26}[a.workload]
     return a
@@ -295,12 +300,14 @@ def e2e_measure(et, ctx, prim, n_events, n_slabs, steps):
 def serving_measure(geom, args):
     """Continuous batching under a Poisson stream of uneven events (1-1000 primaries of
     mixed types, 0.1-100 GeV each): p50/p99 arrival-to-result latency and sustained
-    track-steps/s, tuned form and the plain sparse single buffer on the same stream."""
+    track-steps/s, tuned form (persistent driver, whatever --driver says: the serving
+    loop runs a few iterations per round, where one launch per round pays most) and the
+    plain sparse single buffer on the same stream."""
     from paper_2302_08252_gb300 import serving
     reqs = serving.poisson_requests(args.serving_rate, args.serving_events)
     out = {"rate_per_s": args.serving_rate, "events": args.serving_events,
            "event_sizes": "primaries per event log-uniform 1-1000, 0.1-100 GeV each"}
-    for name, form, layout, driver, cap in (("tuned", args.form, args.layout, args.driver, 22),
+    for name, form, layout, driver, cap in (("tuned", args.form, args.layout, "persistent", 22),
                                             ("plain", "sparse", "aos", "hostloop", 24)):
         srv = serving.Server(geom, form=form, layout=layout, driver=driver, capacity_log2=cap,
                              max_events=max(1024, args.serving_events), iters_per_round=8)

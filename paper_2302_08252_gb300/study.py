@@ -3,10 +3,12 @@ complete transport of a workload for every track-buffer form, layout and driver.
 
     python -m paper_2302_08252_gb300.study [--workload jittered|mixed|uneven|uneven32|small]
         [--forms dense sparse] [--layouts aos soa aosoa32 aosoa64]
-        [--drivers hostloop persistent graph] [--split 0 1] [--reps 3] [--out FILE]
+        [--drivers hostloop persistent graph hybrid] [--hybrid-tracks-log2 17 21]
+        [--split 0 1] [--reps 3] [--out FILE]
 
 Prints one JSON object per candidate (track-steps/s, best-of-reps seconds) and writes
-the list to --out.  `--split 1` times the split step kernels (transport pass, then
+the list to --out.  The hybrid driver is timed once per threshold 2^k of
+`--hybrid-tracks-log2` (default 2^21).  `--split 1` times the split step kernels (transport pass, then
 per-process interaction passes) of the host-loop, graph and hybrid drivers.  Every
 candidate computes the same histories in strict mode, so only the time differs.  GPU
 required.
@@ -56,6 +58,7 @@ def main(argv=None):
     ap.add_argument("--layouts", nargs="+", default=list(autotune.LAYOUTS))
     ap.add_argument("--drivers", nargs="+", default=["hostloop", "persistent"])
     ap.add_argument("--split", nargs="+", type=int, default=[0], choices=[0, 1])
+    ap.add_argument("--hybrid-tracks-log2", nargs="+", type=int, default=[21])
     ap.add_argument("--block-size", type=int, default=256)
     ap.add_argument("--dense-capacity-log2", type=int, default=22)
     ap.add_argument("--sparse-capacity-log2", type=int, default=24)
@@ -70,16 +73,20 @@ def main(argv=None):
         cap = a.dense_capacity_log2 if form == "dense" else a.sparse_capacity_log2
         for layout in a.layouts:
             for driver in a.drivers:
-                for split in a.split:
+                for split, tk in [(sp, k) for sp in a.split
+                                  for k in (a.hybrid_tracks_log2 if driver == "hybrid" else [0])]:
                     if split and driver == "persistent":
                         continue  # no split form of the persistent kernel
                     kw = {"split": True} if split else {}
+                    if driver == "hybrid":
+                        kw["hybrid_tracks"] = 1 << tk
                     if steps is None:
                         steps = steps_of(geom, prim, n_events, form, layout, driver, cap, **kw)
                     t = autotune.time_config(geom, prim, n_events, form, layout, a.block_size,
                                              driver, reps=a.reps, capacity_log2=cap, **kw)
                     r = {"workload": a.workload, "form": form, "layout": layout,
                          "driver": driver, "split": bool(split), "block_size": a.block_size,
+                         "hybrid_tracks": kw.get("hybrid_tracks", 0),
                          "seconds": t, "steps": steps, "track_steps_per_s": steps / t}
                     rows.append(r)
                     print(json.dumps(r), flush=True)

@@ -104,6 +104,34 @@ def test_aosoa128_needs_a_full_block(libet):
     assert et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h)) == et.ET_ERR_INVALID
 
 
+def test_split_interactions_validation(libet):
+    """The split step kernels exist for the host-loop, graph and hybrid drivers, without
+    instrumentation: other combinations are refused before any device work."""
+    import torch
+    from paper_2302_08252_gb300 import et
+
+    def status(**kw):
+        cfg = et.et_config()
+        cfg.capacity_log2 = 10
+        cfg.form = 1
+        cfg.max_events = 1
+        cfg.block_size = 256
+        for k, v in kw.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        st = et.lib.et_create(ctypes.byref(cfg), ctypes.byref(h))
+        if h.value:
+            et.lib.et_destroy(h)
+        return st
+
+    assert status(split_interactions=1, driver=et.DRIVER_PERSISTENT) == et.ET_ERR_INVALID
+    assert status(split_interactions=1, instrument=1) == et.ET_ERR_INVALID
+    assert status(split_interactions=2) == et.ET_ERR_INVALID
+    if not torch.cuda.is_available():  # accepted: creation goes on to the (missing) device
+        for d in (et.DRIVER_HOSTLOOP, et.DRIVER_GRAPH, et.DRIVER_HYBRID):
+            assert status(split_interactions=1, driver=d) == et.ET_ERR_CUDA
+
+
 @pytest.mark.parametrize("layout", ["aos", "soa", "aosoa8", "aosoa16", "aosoa32", "aosoa64",
                                     "aosoa128", "hotcold"])
 def test_layout_mappings_tile_the_buffer(layout):
