@@ -1183,7 +1183,8 @@ et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
   // the grid barrier restarts from zero (the grid may differ on another GPU); launch-local
   // fields are set by the next run
   DevCtl* d = c->d_ctl;
-  CUDA_TRY(c, cudaMemsetAsync(&d->bar_count, 0, sizeof(uint32_t) * 2, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(&d->bar_count, 0, sizeof(uint32_t), c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(&d->bar_gen, 0, sizeof(uint32_t), c->stream));
   CUDA_TRY(c, cudaMemsetAsync(d->grab, 0, sizeof d->grab, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   s = sync_ctl(c);
