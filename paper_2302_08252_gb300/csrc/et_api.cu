@@ -711,7 +711,7 @@ static et_status run_hybrid(et_ctx* c, uint64_t max_iters, et_iter_stats* totals
   for (;;) {
     const uint32_t it = c->h_ctl->iter;
     const uint32_t* row = c->h_ctl->cnt[it % 3];
-    const uint64_t n = (uint64_t)row[0] + row[1] + row[2];
+    const uint64_t n = (uint64_t)row[cw(EM)] + row[cw(EP)] + row[cw(GAM)];
     if (n == 0 || it >= lim) break;
     s = n < c->args.hybrid_t ? launch_persistent(c, lim - it) : launch_graph(c, lim);
     if (s != ET_OK) return s;

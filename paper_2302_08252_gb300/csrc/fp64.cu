@@ -36,7 +36,7 @@ struct alignas(16) Trk {
 static_assert(sizeof(Trk) == 128, "128-byte record");
 
 struct Ctl {
-  uint32_t cnt[3][4];  // word cw(t), rows by iteration % 3 as in the FP32 path
+  uint32_t cnt[3][et::CTL_LINE];  // word cw(t), rows by iteration % 3 as in the FP32 path
   uint32_t iter, status;
   unsigned long long steps[3], secondaries[3];
 };

@@ -97,7 +97,7 @@ __device__ __forceinline__ void warp_reserve(uint32_t packed, uint32_t lane, uin
       b0 = (uint32_t)old;
       b2 = (uint32_t)(old >> 32);
     }
-    if (np) b1 = atomicAdd(row + 2, np);
+    if (np) b1 = atomicAdd(row + cw(EP), np);
   }
   p0 = __shfl_sync(FULL, b0, 0) + (excl & 1023u);
   p1 = __shfl_sync(FULL, b1, 0) + ((excl >> 10) & 1023u);
@@ -713,10 +713,10 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
   }
   if (it >= a.max_iters && !a.iter_log_wrap) c->status |= ST_ITER_LOG_FULL;
   free_ring_boundary(c);
-  for (int t = 0; t < NTYPES; ++t) c->cnt[cur][t] = 0;
+  for (int t = 0; t < NTYPES; ++t) c->cnt[cur][cw(t)] = 0;
   for (int q = 0; q < N_IQ; ++q) c->iq_n[q] = 0;  // split form: the queues are consumed
   c->iter = it + 1;
-  const uint32_t left = c->cnt[nxt][0] + c->cnt[nxt][1] + c->cnt[nxt][2];
+  const uint32_t left = c->cnt[nxt][cw(EM)] + c->cnt[nxt][cw(EP)] + c->cnt[nxt][cw(GAM)];
   const bool stop = left == 0 || c->status != 0 || it + 1 >= c->stop_iter ||
                     (a.hybrid_t != 0 && left < a.hybrid_t);
   c->done = stop ? 1u : 0u;
@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       if (a.iter_ns && it < a.max_iters) a.iter_ns[it] = global_ns();
       for (int t = 0; t < 3; ++t) {
-        c->cnt[(it + 2) % 3][t] = 0;
+        c->cnt[(it + 2) % 3][cw(t)] = 0;
         c->steps[t] += s_n[t];
         const uint32_t li = a.iter_log_wrap ? it % a.max_iters : it;
         if (li < a.max_iters) a.counts_log[(size_t)li * 3 + t] = s_n[t];
@@ -902,9 +902,10 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->iter = it;
     const uint32_t cur = it % 3;
-    for (int t = 0; t < 3; ++t) c->cnt[(it + 2) % 3][t] = 0;  // between iterations only cur is non-zero
+    for (int t = 0; t < 3; ++t) c->cnt[(it + 2) % 3][cw(t)] = 0;  // between iterations only cur is non-zero
     for (int t = 0; t < 3; ++t) c->grab[t] = 0u;
-    c->done =(__ldcg(&c->cnt[cur][0]) + __ldcg(&c->cnt[cur][1]) + __ldcg(&c->cnt[cur][2]) == 0);
+    c->done = (__ldcg(&c->cnt[cur][cw(EM)]) + __ldcg(&c->cnt[cur][cw(EP)]) +
+               __ldcg(&c->cnt[cur][cw(GAM)]) == 0);
   }
 }
 

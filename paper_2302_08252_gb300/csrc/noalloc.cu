@@ -212,7 +212,7 @@ extern "C" et_status et_transport_noalloc(
   if (out.status & ST_BAD_PRIMARY)
     return na_fail(err, err_len, ET_ERR_INVALID, "et_transport_noalloc: invalid primary (skipped)");
   const uint32_t cur = out.iter % 3;
-  if (out.status || out.cnt[cur][0] + out.cnt[cur][1] + out.cnt[cur][2] != 0)
+  if (out.status || out.cnt[cur][cw(EM)] + out.cnt[cur][cw(EP)] + out.cnt[cur][cw(GAM)] != 0)
     return na_fail(err, err_len, ET_ERR_CAPACITY,
                    "et_transport_noalloc: tracks left after ET_NOALLOC_MAX_ITERS iterations");
   if (steps_out) *steps_out = out.steps[0] + out.steps[1] + out.steps[2];
