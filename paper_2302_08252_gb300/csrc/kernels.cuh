@@ -823,6 +823,11 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
     }
   }
   uint32_t bar_gen = threadIdx.x == 0 ? *(volatile uint32_t*)&c->bar_gen : 0u;
+  // block 0's copy of the dense form's peak fill: it only stores, so that its thread 0
+  // (lane 0 of the warp that takes a small iteration's first chunk) waits on no load
+  __shared__ uint32_t s_hwm[3];
+  if (DENSE && blockIdx.x == 0 && threadIdx.x == 0)
+    for (int t = 0; t < 3; ++t) s_hwm[t] = c->hwm[cw(t)];
   bool first = true;
   Tally tl;  // flushed when the loop ends
   tally_reset(tl);
@@ -836,6 +841,16 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       const uint32_t st = first ? 0u : *(volatile uint32_t*)snap;
       const uint32_t tot = s_n[0] + s_n[1] + s_n[2];
       s_stop = tot == 0 || it >= stop_iter || st != 0 || (a.hybrid_t != 0 && tot >= a.hybrid_t);
+      // an iteration's counts are the fill of the one before (the launch's first counts
+      // were recorded by the launch before, or come from injection)
+      if (DENSE && blockIdx.x == 0 && !first) {
+        for (int t = 0; t < 3; ++t) {
+          if (s_n[t] > s_hwm[t]) {
+            s_hwm[t] = s_n[t];
+            c->hwm[cw(t)] = s_n[t];
+          }
+        }
+      }
     }
     __syncthreads();
     first = false;
@@ -845,7 +860,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       if (a.iter_ns && it < a.max_iters) a.iter_ns[it] = global_ns();
       for (int t = 0; t < 3; ++t) {
         c->cnt[(it + 2) % 3][cw(t)] = 0;
-        c->steps[t] += s_n[t];
+        atomicAdd(&c->steps[t], (unsigned long long)s_n[t]);  // a reduction: nothing waits
         const uint32_t li = a.iter_log_wrap ? it % a.max_iters : it;
         if (li < a.max_iters) a.counts_log[(size_t)li * 3 + t] = s_n[t];
       }
@@ -890,12 +905,6 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, batch, drain_all, tl);
     }
     if (!grid_sync(c, gridDim.x, a.timeout_ns, snap, bar_gen, a.free_ring[0] != nullptr)) return;
-    if (DENSE && blockIdx.x == 0 && threadIdx.x == 0) {
-      for (int t = 0; t < 3; ++t) {
-        const uint32_t fill = __ldcg(&c->cnt[(it + 1) % 3][cw(t)]);
-        if (fill > c->hwm[cw(t)]) c->hwm[cw(t)] = fill;
-      }
-    }
     ++it;
   }
   tally_flush(a, tl, lane);

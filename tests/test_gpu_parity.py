@@ -101,6 +101,25 @@ def test_hybrid_driver_full_jittered(geom):
     assert_strict_parity(g, o)
 
 
+@pytest.mark.parametrize("driver", ["hostloop", "graph", "persistent", "hybrid"])
+def test_dense_slot_high_water_is_the_peak_fill(geom, small_ref, driver):
+    """Dense form: the reported high-water mark per type is the largest number of tracks any
+    iteration wrote to the next buffer, i.e. the maximum of the counts log after the
+    first (injected) row -- on every driver, also when the run is done in slices."""
+    from paper_2302_08252_gb300 import et
+    p, o = small_ref
+    ctx = et.make_context(geom, max_events=16, capacity_log2=16, form=et.FORM_DENSE,
+                          layout="aosoa32", driver=driver, hybrid_tracks=300)
+    et.et_inject(ctx, p)
+    et.et_run_until_empty(ctx, 17)
+    et.et_run_until_empty(ctx, 40)
+    et.et_run_until_empty(ctx)
+    counts = et.et_read_iteration_counts(ctx).astype(np.int64)
+    assert np.array_equal(counts, o["counts"].astype(np.int64))
+    expect = counts[1:].max(axis=0)  # e-, e+, gamma
+    assert et.et_read_counters(ctx)["slot_high_water"] == [int(x) for x in expect]
+
+
 def test_empty_run_and_invalid_input(geom):
     from paper_2302_08252_gb300 import et
     ctx = et.make_context(geom, max_events=4, capacity_log2=10)
