@@ -176,6 +176,15 @@ __device__ __forceinline__ void balance(const Trk& t, float E, StepOut& o) {
   }
 }
 
+// Whether the distance num / den (den > 0) can be below the running minimum s.  False
+// only when num >= 2 s den with 2 s den a normal number: the exact quotient is then at
+// least 2 s (1 - 2^-24) > s, so its rounded value is >= s and the comparison it would
+// enter (quotient < s) is false.  Skipping that division leaves the step unchanged.
+__device__ __forceinline__ bool may_limit(float num, float den, float s) {
+  const float bound = 2.0f * s * den;
+  return !(num >= bound && bound >= 0x1p-100f);
+}
+
 // Returns true when a discrete interaction is due: the step is then unfinished
 // (step counter and flags unchanged) and cx holds what interact() needs.
 // `type` is warp-uniform; a compile-time constant at the per-type kernels' call sites.
@@ -210,35 +219,47 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
     const float2 b = tb.tot[m * NBINS + bin];
     sig = b.x + f * b.y;
   }
-  const float s_phys = (sig > 0.0f) ? t.nia / sig : F_INF;
-
   // geometry: slab planes along z, box faces along x and y
-  float zpl = 0.0f, sz, sx, sy;
+  float zpl = 0.0f, sz;
   if (t.dz > 0.0f) { zpl = tb.planes[s0 + 1]; sz = (zpl - t.z) / t.dz; }
   else if (t.dz < 0.0f) { zpl = tb.planes[s0]; sz = (zpl - t.z) / t.dz; }
   else sz = F_INF;
   if (sz < 0.0f) sz = 0.0f;
-  if (t.dx > 0.0f) sx = (half - t.x) / t.dx;
-  else if (t.dx < 0.0f) sx = (-half - t.x) / t.dx;
-  else sx = F_INF;
-  if (sx < 0.0f) sx = 0.0f;
-  if (t.dy > 0.0f) sy = (half - t.y) / t.dy;
-  else if (t.dy < 0.0f) sy = (-half - t.y) / t.dy;
-  else sy = F_INF;
-  if (sy < 0.0f) sy = 0.0f;
 
-  // step limiter: fixed order, earlier wins ties
+  // step limiter: fixed order, earlier wins ties.  A limiter whose distance (a quotient)
+  // cannot be below the running minimum skips its division (may_limit); the comparisons,
+  // and so the step, are those of computing every distance.
   float s = sz;
   int lim = LIM_Z;
-  if (sx < s) { s = sx; lim = LIM_X; }
-  if (sy < s) { s = sy; lim = LIM_Y; }
+  if (t.dx != 0.0f) {
+    const float num = (t.dx > 0.0f) ? (half - t.x) : (-half - t.x);
+    if (may_limit(t.dx > 0.0f ? num : -num, fabsf(t.dx), s)) {
+      float sx = num / t.dx;
+      if (sx < 0.0f) sx = 0.0f;
+      if (sx < s) { s = sx; lim = LIM_X; }
+    }
+  }
+  if (t.dy != 0.0f) {
+    const float num = (t.dy > 0.0f) ? (half - t.y) : (-half - t.y);
+    if (may_limit(t.dy > 0.0f ? num : -num, fabsf(t.dy), s)) {
+      float sy = num / t.dy;
+      if (sy < 0.0f) sy = 0.0f;
+      if (sy < s) { s = sy; lim = LIM_Y; }
+    }
+  }
   float dedx = 0.0f;
   if (charged) {
     dedx = tb.dedx[m];
-    const float sl = (E > 1.0f) ? (LOSS_FRAC * E) / dedx : E / dedx;
-    if (sl < s) { s = sl; lim = LIM_LOSS; }
+    const float num = (E > 1.0f) ? LOSS_FRAC * E : E;
+    if (may_limit(num, dedx, s)) {
+      const float sl = num / dedx;
+      if (sl < s) { s = sl; lim = LIM_LOSS; }
+    }
   }
-  if (s_phys < s) { s = s_phys; lim = LIM_PHYS; }
+  if (sig > 0.0f && may_limit(t.nia, sig, s)) {
+    const float s_phys = t.nia / sig;
+    if (s_phys < s) { s = s_phys; lim = LIM_PHYS; }
+  }
 
   // move
   t.x = t.x + s * t.dx;
