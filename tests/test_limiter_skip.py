@@ -18,11 +18,12 @@ def test_skipped_quotients_never_beat_the_minimum():
     # magnitudes over the whole normal range, plus values straddling the bound
     s = (10.0 ** rng.uniform(-30, 30, n)).astype(F)
     den = (10.0 ** rng.uniform(-30, 30, n)).astype(F)
-    bound = F(2.0) * s * den
-    scale = F(1.0) + rng.uniform(-1e-6, 1e-6, n).astype(F)
-    num = np.where(rng.random(n) < 0.5, bound * scale, (10.0 ** rng.uniform(-30, 30, n)).astype(F))
-    num = np.nextafter(num, np.where(rng.random(n) < 0.5, F(0), F(np.inf))).astype(F)
     with np.errstate(over="ignore", under="ignore", invalid="ignore", divide="ignore"):
+        bound = F(2.0) * s * den
+        scale = F(1.0) + rng.uniform(-1e-6, 1e-6, n).astype(F)
+        num = np.where(rng.random(n) < 0.5, bound * scale,
+                       (10.0 ** rng.uniform(-30, 30, n)).astype(F))
+        num = np.nextafter(num, np.where(rng.random(n) < 0.5, F(0), F(np.inf))).astype(F)
         skip = ~may_limit(num, den, s)
         q = num / den
     ok = np.isfinite(s) & np.isfinite(den) & (den > 0) & np.isfinite(num)
