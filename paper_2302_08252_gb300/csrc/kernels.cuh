@@ -279,13 +279,14 @@ __device__ __forceinline__ View<L, INSTR> view_of(const Args& a, int type, int h
 }
 
 // ---- per-warp interaction queue ----
-// Lanes whose step ends in a discrete interaction park (post-transport track,
-// interaction context, slot) in a shared-memory ring of QCAP entries per warp,
-// stored field-major so that 32 lanes touch 32 consecutive words.  Whenever 32
-// entries wait, the warp drains them with every lane busy; a partial queue is
-// drained when the warp moves to another particle type or runs out of chunks.
-// This keeps the long interaction code (Compton rejection, rotations, pair,
-// brems) from running with most lanes of a warp idle.
+// Photon lanes whose step ends in a discrete interaction park (post-transport track,
+// interaction context, slot) in a shared-memory ring of QCAP entries per warp, stored
+// field-major so that 32 lanes touch 32 consecutive words.  Whenever 32 entries wait,
+// the warp drains them with every lane busy; a partial queue is drained when the warp
+// moves to another particle type or runs out of chunks.  This keeps the long Compton
+// sampler (rejection loop, rotation) from running with most lanes of a warp idle.  The
+// same record layout, with the queue capacity as leading dimension, serves the global
+// per-process queues of the split step kernels.
 constexpr uint32_t QCAP = 64;
 constexpr uint32_t QW = 24;  // 16 track words, 7 context words, slot
 
