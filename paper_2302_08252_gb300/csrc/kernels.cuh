@@ -735,7 +735,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Grid barrier of the persistent kernel.  Every block's thread 0 announces its arrival
 // with a release reduction on a counter that only grows (nblocks per barrier); block 0's
 // thread 0 waits (acquire) until the counter reaches nblocks * (gen + 1), takes the
-// status snapshot that every block's next decision uses, moves the sparse form's
+// status snapshot that every block's next decision uses (read along with the polls), moves the sparse form's
 // slot-reuse ring boundary (`rings`) while every other block waits, and publishes the
 // next generation (release); the others wait (acquire) for it.  `gen` is thread 0's
 // copy of the generation, read once at kernel start (it cannot move before every block
@@ -752,8 +752,15 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
     const unsigned long long t0 = global_ns();
     if (blockIdx.x == 0) {
       const uint32_t target = nblocks * (g + 1u);
+      // the status word is read with every poll, issued before the acquire so that both
+      // loads are in flight together: the snapshot costs no round trip after the last
+      // arrival.  It may miss a bit set just before that arrival; the bits are sticky, so
+      // the next barrier's snapshot has it and the launch stops one iteration later (every
+      // block still takes the same decision, and an error is still reported)
+      uint32_t st_seen = 0u;
       for (;;) {
         uint32_t v;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(st_seen) : "l"(&c->status) : "memory");
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&c->bar_count) : "memory");
         if ((int32_t)(v - target) >= 0) break;
         if (global_ns() - t0 > timeout_ns) {
@@ -763,7 +770,7 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
         }
       }
       if (ok) {
-        *snap_status = *(volatile uint32_t*)&c->status;
+        *snap_status = st_seen;
         if (rings) free_ring_boundary(c);
         asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&c->bar_gen), "r"(g + 1u) : "memory");
       }
