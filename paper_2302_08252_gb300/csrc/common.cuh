@@ -93,9 +93,8 @@ struct alignas(128) DevCtl {
   unsigned long long idlog_n;
   alignas(128) uint32_t hwm[4];  // word cw(t) -- sparse: slots handed out; dense: peak next fill
   alignas(128) uint32_t bar_count;  // grid barrier (persistent driver)
-  alignas(128) uint32_t bar_gen;
-  alignas(128) uint32_t status_snap;  // status as seen by the last grid barrier
-  uint32_t n_done;              // serving: events completed so far (completion ring position)
+  alignas(128) uint32_t bar_gen;  // generation << 1 | (status non-zero at that barrier)
+  alignas(128) uint32_t n_done;  // serving: events completed so far (completion ring position)
   // sparse slot reuse, per type (monotone counters; ring index = value % cap): slots in
   // [free_head, free_snap) may be taken in this iteration, slots freed in this iteration
   // are appended at free_tail and become takeable at the next iteration boundary

@@ -734,29 +734,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Grid barrier of the persistent kernel.  Every block's thread 0 announces its arrival
 // with a release reduction on a counter that only grows (nblocks per barrier); block 0's
-// thread 0 waits (acquire) until the counter reaches nblocks * (gen + 1), takes the
-// status snapshot that every block's next decision uses (read along with the polls), moves the sparse form's
-// slot-reuse ring boundary (`rings`) while every other block waits, and publishes the
-// next generation (release); the others wait (acquire) for it.  `gen` is thread 0's
-// copy of the generation, read once at kernel start (it cannot move before every block
-// has arrived at the first barrier).  Every wait is bounded: on timeout the block sets
+// thread 0 waits (acquire) until the counter reaches nblocks * (gen + 1), moves the
+// sparse form's slot-reuse ring boundary (`rings`) while every other block waits, and
+// publishes the next generation (release); the others wait (acquire) for it.  The
+// published word carries the generation (bits 1..31) and whether the status word was
+// non-zero (bit 0), the snapshot that every block's next decision uses: it travels with
+// the generation, so no other write has to complete before the release.  The status is
+// loaded with every poll of the counter (issued before the acquire, both loads in
+// flight); a bit set just before the last arrival is seen one barrier later -- the bits
+// are sticky, every block still takes the same decision, and the error is reported.
+// `gen` is thread 0's copy of the generation count, read once at kernel start (it cannot
+// move before every block has arrived at the first barrier).  The stop flag goes to
+// `stop_out` (shared memory).  Every wait is bounded: on timeout the block sets
 // ST_TIMEOUT and the function returns false.
 static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long timeout_ns,
-                                 uint32_t* snap_status, uint32_t& gen, bool rings) {
+                                 uint32_t& gen, bool rings, uint32_t* stop_out) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     const uint32_t g = gen;
     int ok = 1;
+    uint32_t stop = 0u;
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&c->bar_count) : "memory");
     const unsigned long long t0 = global_ns();
     if (blockIdx.x == 0) {
       const uint32_t target = nblocks * (g + 1u);
-      // the status word is read with every poll, issued before the acquire so that both
-      // loads are in flight together: the snapshot costs no round trip after the last
-      // arrival.  It may miss a bit set just before that arrival; the bits are sticky, so
-      // the next barrier's snapshot has it and the launch stops one iteration later (every
-      // block still takes the same decision, and an error is still reported)
       uint32_t st_seen = 0u;
       for (;;) {
         uint32_t v;
@@ -770,15 +772,20 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
         }
       }
       if (ok) {
-        *snap_status = st_seen;
+        stop = st_seen != 0u ? 1u : 0u;
         if (rings) free_ring_boundary(c);
-        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&c->bar_gen), "r"(g + 1u) : "memory");
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&c->bar_gen), "r"(((g + 1u) << 1) | stop)
+                     : "memory");
       }
     } else {
+      const uint32_t gw = g & 0x7fffffffu;
       for (;;) {
         uint32_t v;
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&c->bar_gen) : "memory");
-        if (v != g) break;
+        if ((v >> 1) != gw) {
+          stop = v & 1u;
+          break;
+        }
         if (global_ns() - t0 > timeout_ns) {
           atomicOr(&c->status, ST_TIMEOUT);
           ok = 0;
@@ -787,6 +794,7 @@ static __device__ bool grid_sync(DevCtl* c, uint32_t nblocks, unsigned long long
       }
     }
     gen = g + 1u;
+    *stop_out = stop;
     ok_s = ok;
   }
   __syncthreads();
@@ -810,7 +818,6 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
   const Tabs tb = stage_tables<true, true>(smem, a);
   WarpQueue wq = warp_queue(smem, (int)a.n_mat);
   DevCtl* c = a.ctl;
-  uint32_t* snap = &c->status_snap;
   const uint32_t lane = threadIdx.x & 31u;
   // two warp numberings: block-major for large iterations; block-first for small ones, so
   // that their few chunks land on different SMs instead of sharing the schedulers of
@@ -830,7 +837,9 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       c->run_sec0[t] = c->secondaries[t];
     }
   }
-  uint32_t bar_gen = threadIdx.x == 0 ? *(volatile uint32_t*)&c->bar_gen : 0u;
+  // the generation count (the published word holds it shifted left by one)
+  uint32_t bar_gen = threadIdx.x == 0 ? (*(volatile uint32_t*)&c->bar_gen) >> 1 : 0u;
+  __shared__ uint32_t s_snap_stop;
   // block 0's copy of the dense form's peak fill: it only stores, so that its thread 0
   // (lane 0 of the warp that takes a small iteration's first chunk) waits on no load
   __shared__ uint32_t s_hwm[3];
@@ -846,7 +855,7 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       // the first decision uses only what the launch started with (the same in every
       // block: a block that starts late must not see a status bit set by another block's
       // first iteration); later ones use the snapshot taken at the barrier
-      const uint32_t st = first ? 0u : *(volatile uint32_t*)snap;
+      const uint32_t st = first ? 0u : s_snap_stop;
       const uint32_t tot = s_n[0] + s_n[1] + s_n[2];
       s_stop = tot == 0 || it >= stop_iter || st != 0 || (a.hybrid_t != 0 && tot >= a.hybrid_t);
       // an iteration's counts are the fill of the one before (the launch's first counts
@@ -912,7 +921,8 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
       }
       process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, batch, drain_all, tl);
     }
-    if (!grid_sync(c, gridDim.x, a.timeout_ns, snap, bar_gen, a.free_ring[0] != nullptr)) return;
+    if (!grid_sync(c, gridDim.x, a.timeout_ns, bar_gen, a.free_ring[0] != nullptr, &s_snap_stop))
+      return;
     ++it;
   }
   tally_flush(a, tl, lane);
