@@ -67,3 +67,19 @@ def test_reference_arm_runs_on_rank_zero_only():
     d = json.loads(lines[0][0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.parametrize("argv,workload,driver,cap", [
+    ([], "jittered", "persistent", 22),
+    (["--config", "1"], "small", "persistent", 16),
+    (["--config", "3"], "mixed", "hybrid", 24),
+    (["--config", "4"], "uneven", "hybrid", 26),
+    (["--config", "4", "--driver", "graph", "--capacity-log2", "25"], "uneven", "graph", 25),
+])
+def test_bench_workload_defaults(argv, workload, driver, cap):
+    """Configuration numbers pick the workload; the driver and capacity default per
+    workload (the fastest measured driver) unless given."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.parse_args(argv)
+    assert (a.workload, a.driver, a.capacity_log2) == (workload, driver, cap)
