@@ -17,7 +17,8 @@
 // Deposits: one fire-and-forget FP64 reduction per lane into score[event][slab];
 // the rarer ledger terms (below cut, escaped, mass created/consumed) likewise.
 // The step kernels return at once when the device status word is non-zero; the
-// persistent kernel stops at the next iteration boundary.
+// persistent kernel stops at the next iteration boundary (or the one after, when the bit
+// was set just before the last block arrived at the barrier).
 #pragma once
 
 #include <cuda/atomic>
