@@ -310,7 +310,7 @@ def serving_measure(geom, args):
     for name, form, layout, driver, cap in (("tuned", args.form, args.layout, "persistent", 22),
                                             ("plain", "sparse", "aos", "hostloop", 24)):
         srv = serving.Server(geom, form=form, layout=layout, driver=driver, capacity_log2=cap,
-                             max_events=max(1024, args.serving_events), iters_per_round=8)
+                             max_events=max(1024, args.serving_events), iters_per_round=16)
         st = srv.serve(reqs)
         q = st.latency_quantiles()
         out[name] = {"form": form, "layout": layout, "driver": driver,

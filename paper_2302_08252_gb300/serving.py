@@ -74,7 +74,7 @@ def reserve(primaries: np.ndarray) -> np.ndarray:
 class Server:
     def __init__(self, geom: dict, form: str = "dense", layout: str = "aos",
                  driver: str = "persistent", capacity_log2: int = 22, max_events: int = 1 << 14,
-                 iters_per_round: int = 8, seed: int = 1, tables: dict | None = None):
+                 iters_per_round: int = 16, seed: int = 1, tables: dict | None = None):
         self.geom = geom
         self.n_slabs = len(geom["thickness"])
         self.capacity = 1 << capacity_log2

@@ -24,7 +24,7 @@ FORMS = {"tuned": ("dense", "aosoa32", "persistent"), "plain": ("sparse", "aos",
 
 
 def run(rate: float, n_events: int, max_primaries: int, warmup_frac: float, form_key: str,
-        capacity_log2: int = 24, tuned_driver: str = "persistent", iters_per_round: int = 8) -> dict:
+        capacity_log2: int = 24, tuned_driver: str = "persistent", iters_per_round: int = 16) -> dict:
     form, layout, driver = FORMS[form_key]
     if form_key == "tuned":
         driver = tuned_driver
@@ -57,7 +57,7 @@ def main(argv=None):
     ap.add_argument("--forms", nargs="+", default=["tuned", "plain"])
     ap.add_argument("--tuned-driver", default="persistent",
                     choices=["persistent", "graph", "hostloop", "hybrid"])
-    ap.add_argument("--iters-per-round", type=int, default=8)
+    ap.add_argument("--iters-per-round", type=int, default=16)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     rows = []
