@@ -8,8 +8,11 @@ injects `-particles 25 -batch 5`), small buffers.  Writes into --out:
   slots_<form>_<type>.png                         per-track-slot counts (slot utilisation)
   trace_<form>_<layout>.txt                       reads and writes per field and type
   summary.json                                    slots used, max counts per type, ...
+With --full-trace, also the field trace of the whole 1,000 x 10 GeV jittered workload
+(persistent driver; dense AoSoA-32 and sparse AoS):
+  trace_full_<form>_<layout>.txt
 
-Usage: python -m paper_2302_08252_gb300.instrument_report --out DIR
+Usage: python -m paper_2302_08252_gb300.instrument_report --out DIR [--full-trace]
 """
 from __future__ import annotations
 
@@ -75,11 +78,29 @@ def run(form: str, layout: str, capacity_log2: int, out: str, prim: np.ndarray) 
     return res
 
 
+def full_trace(form: str, layout: str, capacity_log2: int, out: str) -> dict:
+    """Per-field reads and writes over the whole jittered workload (one run)."""
+    geom = W.calorimeter()
+    prim = W.jittered_electrons()
+    ctx = et.make_context(geom, max_events=len(prim), capacity_log2=capacity_log2,
+                          form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
+                          layout=layout, driver="persistent", instrument=True)
+    et.et_inject(ctx, prim)
+    r = et.et_run_until_empty(ctx)
+    tr = et.et_read_field_trace(ctx)
+    with open(os.path.join(out, f"trace_full_{form}_{layout}.txt"), "w") as f:
+        f.write(heatmap.trace_table(tr) + "\n")
+    return {"steps": int(r["steps"]), "iterations": int(r["iterations"]),
+            "trace": tr.astype(int).tolist()}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
     ap.add_argument("--sparse-capacity-log2", type=int, default=23)
     ap.add_argument("--dense-capacity-log2", type=int, default=17)
+    ap.add_argument("--full-trace", action="store_true",
+                    help="also trace the whole 1,000 x 10 GeV jittered workload")
     args = ap.parse_args(argv)
     os.makedirs(args.out, exist_ok=True)
     prim = heatmap_workload()
@@ -91,9 +112,15 @@ def main(argv=None):
         heatmap.layout_svg(os.path.join(args.out, f"layout_{form}_aos.svg"), "aos")
     heatmap.layout_svg(os.path.join(args.out, "layout_soa.svg"), "soa", cap=4)
     heatmap.layout_svg(os.path.join(args.out, "layout_aosoa32.svg"), "aosoa32", n_tracks=2)
+    if args.full_trace:
+        summary["full_dense_aosoa32"] = full_trace("dense", "aosoa32", 21, args.out)
+        summary["full_sparse_aos"] = full_trace("sparse", "aos", 24, args.out)
     with open(os.path.join(args.out, "summary.json"), "w") as f:
         json.dump(summary, f, indent=1)
     for k, v in summary.items():
+        if k.startswith("full_"):
+            print(k, "steps", v["steps"], "iterations", v["iterations"])
+            continue
         print(k, "steps", v["steps"], "slots", v["slots_high_water"], "max", v["max_word_count"],
               "front", [round(x, 3) for x in v["front_fraction"]])
 
