@@ -149,6 +149,65 @@ def test_annihilation_at_rest(oworld):
         assert r["dep_cont"] == float(np.float32(0.5))    # the whole kinetic energy
 
 
+def _block_uniforms(track_id: int, step: int, block: int, seed: int = 1, event: int = 0):
+    """The four uniforms of Philox block `block` of a track's step, from the KAT-pinned
+    Philox and the endpoint-pinned u01 conversion (the keying of the toy model's draws)."""
+    ctr = np.array([[track_id & 0xFFFFFFFF, track_id >> 32, step, block]], dtype=np.uint32)
+    return [oracle.u01(int(x)) for x in oracle.philox(ctr, (seed, event))[0]]
+
+
+def test_pair_energy_share_uniform(oworld):
+    # a 1 GeV photon in lead almost always pair-produces; the electron's share of the
+    # kinetic energy left after the two rest masses is uniform on [0, 1] and comes from
+    # the third uniform of the step's draw block
+    e = np.float32(1000.0)
+    avail = np.float32(e - np.float32(2 * MC2))
+    share, n_pair = [], 0
+    for i in range(12000):
+        r = oracle.step_one(oworld, W.GAMMA, _photon(oworld, float(e), id=i))
+        if r["proc"] != oracle.PROC_PAIR:
+            continue
+        n_pair += 1
+        em = [s["e"] for s, ty in zip(r["sec"], r["sec_type"]) if ty == W.E_MINUS]
+        if not em:  # electron below the cut: its energy went to the below-cut tally
+            continue
+        u = _block_uniforms(i, 0, 0)
+        assert em[0] == np.float32(np.float32(u[2]) * avail), i
+        share.append(float(em[0]) / float(avail))
+    assert n_pair >= 10000
+    assert stats.kstest(share, "uniform").pvalue > 1e-3
+    # the share does not depend on the process-selection draw (a reused u1 would
+    # confine it to the pair's sub-interval of [0, 1])
+    lo = np.asarray(share) < 0.5
+    assert 0.45 < lo.mean() < 0.55
+
+
+def test_annihilation_angles_isotropic(oworld):
+    # the photon pair of a positron annihilating at rest is isotropic: cos(theta) uniform on
+    # [-1, 1], phi uniform on [0, 2 pi), the two independent; drawn from block 65 of the
+    # positron's last step (first uniform -> cos(theta), second -> phi)
+    n = 10000
+    cost = np.empty(n)
+    phi = np.empty(n)
+    for i in range(n):
+        r = oracle.step_one(oworld, W.E_PLUS, _photon(oworld, 0.5, nia=50.0, id=i))
+        assert r["nsec"] == 2
+        a = r["sec"][0]
+        cost[i] = float(a["dz"])
+        phi[i] = np.arctan2(float(a["dy"]), float(a["dx"])) % (2 * np.pi)
+        u = _block_uniforms(i, 0, 65)
+        assert a["dz"] == np.float32(np.float32(2.0) * np.float32(u[0]) - np.float32(1.0)), i
+        d = abs(phi[i] - 2 * np.pi * u[1])
+        if abs(float(a["dz"])) < 0.999:  # phi is ill-defined at the poles
+            assert min(d, 2 * np.pi - d) < 1e-4, (i, phi[i], u[1])
+    assert stats.kstest(cost, "uniform", args=(-1.0, 2.0)).pvalue > 1e-3
+    assert stats.kstest(phi, "uniform", args=(0.0, 2 * np.pi)).pvalue > 1e-3
+    # independence: chi-square of the 5 x 5 contingency table of (cos theta, phi)
+    h, _, _ = np.histogram2d(cost, phi, bins=[np.linspace(-1, 1, 6),
+                                             np.linspace(0, 2 * np.pi, 6)])
+    assert stats.chi2_contingency(h)[1] > 1e-3
+
+
 def test_geometry_limits(oworld):
     # photon along +z from the front face: stops exactly on the first plane, enters slab 1
     tr = oracle.make_track(z=0.0, d=(0.0, 0.0, 1.0), e=1.0, nia=1e6, slab=0)
