@@ -2,16 +2,19 @@
 """Benchmark of the EM shower transport hot path (one JSON line on rank 0).
 
 A step is one complete transport run of the workload (reset, inject, iterate until no
-track is left): 1,000 electrons of 10 GeV with 1 mrad direction jitter into the 50-layer
-Pb/lAr calorimeter (92.1 M track-steps, 263 iterations), in the tuned form (dense double
-buffer, AoSoA-32, persistent kernel, strict FP32 with FP64 scoring).  Reported:
+track is left).  The default workload is the batched one: 256 events of uneven size
+(1-1,000 primaries each, log-uniform; mixed e-/e+/gamma of 0.1-100 GeV; 41,001 primaries,
+5.36 G track-steps) into the 50-layer Pb/lAr calorimeter, in the tuned form (dense double
+buffer, strict FP32 with FP64 scoring) with the layout, block size and driver the
+autotuner picked for it (tuned.json in the package).  --config 1/2/3 select the small
+gun, the 1,000 x 10 GeV electron shower and the 10,000 mixed primaries.  Reported:
 
   value         track-steps/s, primaries resident in device memory, L2 flushed between steps
   e2e           the same through the C ABI with host buffers (H2D of the primaries and D2H
                 of the scores inside each timed step)
-  roofline      the transport kernel against the HBM roofline: algorithmic bytes per launch
+  roofline      the transport kernels against the HBM roofline: algorithmic bytes per run
                 (64 B read per step + 64 B per survivor + 64 B per secondary = 64 (2 S - P))
-                over its CUDA-event duration, against the measured copy bandwidth
+                over their CUDA-event duration, against the measured copy bandwidth
   plain         the plain form (sparse single buffer, AoS, host loop) on the same workload
   cpu_baseline  the CPU oracle on the host cores
 
@@ -48,17 +51,18 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="jittered", choices=["jittered", "small", "mixed", "uneven"])
+    ap.add_argument("--workload", default="uneven", choices=["jittered", "small", "mixed", "uneven"])
     ap.add_argument("--config", type=int, default=None, choices=[1, 2, 3, 4],
-                    help="the workload by number: 1 small, 2 jittered (default), 3 mixed, 4 uneven")
-    ap.add_argument("--form", default="dense", choices=["dense", "sparse"])
-    ap.add_argument("--layout", default="aosoa32", choices=["aos", "soa", "aosoa8", "aosoa16", "aosoa32",
-                                                         "aosoa64", "aosoa128", "hotcold"])
+                    help="the workload by number: 1 small, 2 jittered, 3 mixed, 4 uneven (default)")
+    ap.add_argument("--form", default=None, choices=["dense", "sparse"])
+    ap.add_argument("--layout", default=None, choices=["aos", "soa", "aosoa8", "aosoa16", "aosoa32",
+                                                       "aosoa64", "aosoa128", "hotcold"],
+                    help="default: the autotuner's pick for the workload, else aosoa32")
     ap.add_argument("--driver", default=None, choices=["hostloop", "graph", "persistent", "hybrid"],
-                    help="default per workload: persistent for the single showers, hybrid for"
-                         " the mixed primaries and the batched events (the fastest measured)")
+                    help="default: the autotuner's pick for the workload, else persistent for"
+                         " the single showers and hybrid for the mixed primaries")
     ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
-    ap.add_argument("--block-size", type=int, default=256)
+    ap.add_argument("--block-size", type=int, default=None)
     ap.add_argument("--capacity-log2", type=int, default=None,
                     help="track slots per type: 2^N (default per workload: 16, 22, 24, 26)")
     ap.add_argument("--plain-steps", type=int, default=2)
@@ -72,9 +76,18 @@ def parse_args(argv=None):
     a = ap.parse_args(argv)
     if a.config is not None:
         a.workload = {1: "small", 2: "jittered", 3: "mixed", 4: "uneven"}[a.config]
+    from paper_2302_08252_gb300 import tuned
+    t = tuned.config(a.workload) or {}
+    a.tuned = bool(t)
+    if a.form is None:
+        a.form = t.get("form", "dense")
+    if a.layout is None:
+        a.layout = t.get("layout", "aosoa32")
+    if a.block_size is None:
+        a.block_size = t.get("block_size", 256)
     if a.driver is None:
-        a.driver = {"small": "persistent", "jittered": "persistent", "mixed": "hybrid",
-                    "uneven": "hybrid"}[a.workload]
+        a.driver = t.get("driver") or {"small": "persistent", "jittered": "persistent",
+                                       "mixed": "hybrid", "uneven": "hybrid"}[a.workload]
     if a.capacity_log2 is None:
         a.capacity_log2 = {"small": 16, "jittered": 22, "mixed": 24, "uneven": 26}[a.workload]
     return a
@@ -321,32 +334,41 @@ def serving_measure(geom, args):
     return out
 
 
-def cpu_baseline(geom, prim, n_events, max_events=None, one_thread_events=50):
-    """The oracle on the host cores: the whole workload, or its first max_events events, on
-    every core; and, under "one_thread", its first one_thread_events events on one thread."""
-    import oracle
+def oracle_sample(workload: str, prim, n_events: int, reference: bool):
+    """A bounded sample of the workload for the oracle (the CPU baseline, about 10-30 s on
+    the host cores; the reference arm, about a second per step).  The batched events are
+    sampled by primaries (every k-th, event numbers kept), so that the sample has the
+    workload's per-primary mix and its events spread over all cores."""
     from paper_2302_08252_gb300 import workloads as W
-    full = prim
-    what = "whole workload"
-    if max_events is not None and n_events > max_events:
-        prim = W.select_events(prim, list(range(max_events)))
-        what = f"first {max_events} of {n_events} events"
+    if workload == "uneven":
+        k = 32 if reference else 4
+        return prim[::k].copy(), f"one primary in {k} of the {len(prim)} (event numbers kept)"
+    if reference and workload in ("jittered", "mixed"):
+        m = 100 if workload == "jittered" else 1000
+        return W.select_events(prim, list(range(min(m, n_events)))), f"first {m} events"
+    return prim, "whole workload"
+
+
+def cpu_baseline(geom, prim, n_events, workload, one_thread_primaries=50):
+    """The oracle on the host cores (a bounded sample of the workload on every core), and
+    under "one_thread" its first one_thread_primaries primaries on one thread."""
+    import oracle
+    sample, what = oracle_sample(workload, prim, n_events, reference=False)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = oracle.run(geom, prim, n_events=n_events, seed=1, nthreads=cores)
+    r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
     dt = time.perf_counter() - t0
     steps = int(r["steps"].sum())
-    k = min(one_thread_events, n_events)
-    sample1 = W.select_events(full, list(range(k)))
+    sample1 = sample[:one_thread_primaries].copy()
     t1 = time.perf_counter()
     r1 = oracle.run(geom, sample1, n_events=n_events, seed=1, nthreads=1)
     dt1 = time.perf_counter() - t1
     steps1 = int(r1["steps"].sum())
     return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{what} ({len(prim)} primaries, {steps} steps) on {cores} threads,"
+            "sample": f"{what} ({len(sample)} primaries, {steps} steps) on {cores} threads,"
                       f" {dt:.2f} s wall",
             "one_thread": {"value": steps1 / dt1, "unit": UNIT, "cores": 1,
-                           "sample": f"first {k} events ({len(sample1)} primaries, {steps1}"
+                           "sample": f"first {len(sample1)} primaries of that sample ({steps1}"
                                      f" steps) on 1 thread, {dt1:.2f} s"}}
 
 
@@ -356,11 +378,9 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    from paper_2302_08252_gb300 import workloads as W
     geom, prim, n_events, desc = make_workload(args.workload, 0)
-    # a bounded sample: about 10^7 track-steps per step on the host cores
-    events = list(range(min(n_events, 4 if args.workload == "uneven" else 100)))
-    sample = W.select_events(prim, events)
+    # a bounded sample: about a second of host-core work per step
+    sample, what = oracle_sample(args.workload, prim, n_events, reference=True)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
@@ -376,10 +396,12 @@ def reference_arm(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": desc, "sample_events": len(events), "mode": "strict",
+        "config": {"workload": desc, "sample": what, "sample_primaries": int(len(sample)),
+                   "mode": "strict",
                    "implementation": "CPU oracle (plain C, depth-first per event)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {len(events)} events per step on {cores} threads"},
+                         "sample": f"{what} per step ({len(sample)} primaries,"
+                                   f" {steps // max(1, args.steps)} steps) on {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -472,10 +494,7 @@ def ours_arm(args, rank, world, group):
         if not args.no_serving:
             line["serving"] = serving_measure(geom, args)
         if not args.no_cpu_baseline:
-            uneven = args.workload == "uneven"
-            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events,
-                                                max_events=32 if uneven else None,
-                                                one_thread_events=1 if uneven else 50)
+            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events, args.workload)
     line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)
     if rank == 0:
         print(json.dumps(line), flush=True)

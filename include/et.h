@@ -80,7 +80,7 @@ typedef struct {
   int32_t mode;             /* ET_MODE_*: strict = bit-exact toy model, fast = intrinsics + FMA */
   int32_t driver;           /* ET_DRIVER_*: how et_run_until_empty iterates */
   int32_t block_size;       /* threads per block of the step kernels (64..256, multiple of 32; 0 = 256) */
-  uint64_t seed;            /* physics seed: Philox key word 0 is its low 32 bits */
+  uint64_t seed;            /* physics seed, below 2^32 (Philox key word 0); larger: ET_ERR_INVALID */
   uint32_t max_events;      /* events are numbered 0..max_events-1 */
   uint32_t max_iters;       /* length of the per-iteration count log */
   int32_t instrument;       /* 1: count per-field reads/writes and per-word accesses */
@@ -309,13 +309,19 @@ et_status et_read_timing(et_ctx* ctx, double* ms_total, uint64_t* launches);
  * not synchronise the device (cudaMalloc/cudaFree may), plug-ins handed a stream and
  * buffers but no allocator.  All scratch (dense double buffers of the three particle
  * types, control block, iteration log, staged geometry and tables) lives in one
- * file-scope device array of ET_NOALLOC_SCRATCH_BYTES, reserved when the library is
- * loaded and held by every GPU that loads it until the process exits.  The call
- * allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ * file-scope device array of ET_NOALLOC_SCRATCH_BYTES, reserved on a device when the
+ * module holding it is loaded there and held by that device until the process exits.
+ * The call allocates nothing itself: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  Under CUDA's lazy module loading (the default) the modules are loaded by
+ * the first call on each device, which reserves the array then and may synchronise;
+ * a caller that needs the guarantee from the very first call sets
+ * CUDA_MODULE_LOADING=EAGER or makes one warm-up call.
  *
  * Inputs: geometry and tables in host memory, as for et_create_geometry and
  * et_load_tables (257 nodes per table); n_primaries records in device memory
- * (16-byte aligned), validated on the device.  Outputs (device memory, zeroed and
+ * (16-byte aligned), validated on the device; seed below 2^32 (the Philox key word).
+ * The sizes of the device buffers cannot be checked here: score_device and
+ * ledger_device must hold n_events rows.  Outputs (device memory, zeroed and
  * written by the call): score_device[n_events][n_slabs] per-slab deposits and
  * ledger_device[n_events][5] = injected, below-cut, escaped, mass created, mass
  * consumed (MeV).  steps_out (host, optional) receives the track steps taken.  The
@@ -324,7 +330,9 @@ et_status et_read_timing(et_ctx* ctx, double* ms_total, uint64_t* launches);
  *
  * Limits: at most ET_NOALLOC_MAX_TRACKS active tracks per type in any iteration (and
  * that many primaries), at most ET_NOALLOC_MAX_ITERS iterations; beyond either the
- * call returns ET_ERR_CAPACITY with a message in err (err_len bytes, may be NULL).
+ * call returns ET_ERR_CAPACITY with a message in err (err_len bytes, may be NULL).  A
+ * primary the device rejects (type, event >= n_events, energy, position) is skipped and
+ * the call returns ET_ERR_INVALID after the others have been transported.
  *
  * The first call on a device looks up the array's device address (once per device,
  * with that device current); make that first call before any stream capture.  Every
@@ -360,8 +368,9 @@ et_status et_transport_noalloc(uint32_t n_slabs, const double* thickness_mm,
  * n primaries; 2^capacity_log2 (6..26) slots per type and buffer.  Outputs (host
  * memory): score_out[n_events][n_slabs] per-slab deposits, ledger_out[n_events][5]
  * (optional) as for et_transport_noalloc, steps_out and iterations_out (optional).
- * Errors: ET_ERR_INVALID for bad arguments or primaries (type, event >= n_events,
- * ekin <= 0, z outside the slabs); ET_ERR_CAPACITY if the primaries or a buffer
+ * Errors: ET_ERR_INVALID for bad arguments (a seed of 2^32 or more among them) or
+ * primaries (type, event >= n_events, ekin <= 0, z outside the slabs);
+ * ET_ERR_CAPACITY if the primaries or a buffer
  * exceed the capacity; ET_ERR_TIMEOUT after 65536 iterations with tracks left;
  * ET_ERR_NOMEM / ET_ERR_CUDA from the runtime.  Uses the current device's default
  * stream.

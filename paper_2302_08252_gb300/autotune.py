@@ -98,7 +98,7 @@ def main(argv=None):
     driver at the default layout on the whole workload (GPU).
 
         python -m paper_2302_08252_gb300.autotune [--workload uneven] [--sample 32]
-            [--capacity-log2 26] [--out FILE]
+            [--capacity-log2 26] [--out FILE] [--write-tuned]
     """
     import argparse
 
@@ -110,6 +110,8 @@ def main(argv=None):
     ap.add_argument("--capacity-log2", type=int, default=26)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--write-tuned", action="store_true",
+                    help="record the pick in tuned.json (the bench's default for the workload)")
     a = ap.parse_args(argv)
     geom = W.calorimeter()
     prim, n_events = study.workload(a.workload)
@@ -133,6 +135,13 @@ def main(argv=None):
     if a.out:
         with open(a.out, "w") as f:
             json.dump(res, f, indent=1)
+    if a.write_tuned:
+        from . import tuned as T
+        n_cand = len(tuned["table"])
+        T.write(a.workload, b, f"{tuned['tuned_on_events']}-event sample of the {a.workload}"
+                f" workload, all {n_cand} candidates, best of {a.reps}",
+                f"python -m paper_2302_08252_gb300.autotune --workload {a.workload}"
+                f" --sample {a.sample} --write-tuned")
     return res
 
 

@@ -203,7 +203,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
       k.layout < 0 || k.layout >= N_LAYOUTS || (k.mode != 0 && k.mode != 1) || k.driver < 0 ||
       (k.layout == LAYOUT_AOSOA128 && k.capacity_log2 < 7) ||
       k.driver > 3 || k.block_size < 64 || k.block_size > 256 || (k.block_size % 32) != 0 ||
-      k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) ||
+      k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) || (k.seed >> 32) != 0 ||
       ((k.alloc == nullptr) != (k.free == nullptr)) ||
       (k.split_interactions != 0 && k.split_interactions != 1) ||
       (k.split_interactions && (k.driver == ET_DRIVER_PERSISTENT || k.instrument)))

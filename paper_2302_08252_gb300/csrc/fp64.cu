@@ -322,7 +322,7 @@ extern "C" et_status et_run_fp64(uint32_t n_slabs, const double* thickness_mm,
   using namespace et64;
   if (n_slabs < 1 || n_slabs > (uint32_t)et::MAX_SLABS || n_materials < 1 || n_materials > 4 ||
       !thickness_mm || !material || !sigma || !dedx || (n && !primaries) || n_events == 0 ||
-      capacity_log2 < 6 || capacity_log2 > 26 || !score_out)
+      capacity_log2 < 6 || capacity_log2 > 26 || !score_out || (seed >> 32) != 0)
     return ET_ERR_INVALID;
   const uint32_t cap = 1u << capacity_log2;
   if (n > cap) return ET_ERR_CAPACITY;

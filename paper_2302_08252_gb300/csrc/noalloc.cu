@@ -7,8 +7,8 @@
 // handed a stream and buffers but no allocator.  For them this entry point keeps all
 // of its scratch -- the dense double buffers of the three particle types, the device
 // control block, the iteration count log and the staged geometry and tables -- in one
-// file-scope device array of fixed size, reserved when the library is loaded and held
-// by every GPU that loads it until the process exits.  The caller passes the inputs
+// file-scope device array of fixed size, reserved when the module holding it is loaded
+// on a device and held by that device until the process exits.  The caller passes the inputs
 // (primaries in device memory, geometry and tables in host memory) and the device
 // output buffers (scores, ledger).
 //
@@ -77,6 +77,7 @@ extern "C" et_status et_transport_noalloc(
   if (n_slabs < 1 || n_slabs > (uint32_t)MAX_SLABS || !thickness_mm || !material ||
       !(half_xy_mm > 0.0f) || n_materials < 1 || n_materials > (uint32_t)MAX_MAT || !sigma ||
       !dedx || !(inv_dlog > 0.0f) || n_events == 0 || !score_device || !ledger_device ||
+      (seed >> 32) != 0 ||
       (n_primaries && !primaries_device) || ((uintptr_t)primaries_device & 15u))
     return na_fail(err, err_len, ET_ERR_INVALID, "et_transport_noalloc: invalid argument");
 

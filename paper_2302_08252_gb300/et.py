@@ -31,6 +31,7 @@ MODE_STRICT, MODE_FAST = 0, 1
 DRIVER_HOSTLOOP, DRIVER_GRAPH, DRIVER_PERSISTENT, DRIVER_HYBRID = range(4)
 DRIVERS = {"hostloop": 0, "graph": 1, "persistent": 2, "hybrid": 3}
 N_LEAVES = 15
+N_TAB, N_NODES = 5, 257   # tables: [material][Compton, pair, photoelectric, total, brems][node]
 LEAF_NAMES = ("x", "y", "z", "dx", "dy", "dz", "ekin", "num_ia_left", "id", "event", "step",
               "slab", "time", "track_len", "flags")
 IDREC_DTYPE = np.dtype([("id", "<u8"), ("steps", "<u4"), ("type_death", "<u4")])
@@ -402,29 +403,74 @@ NOALLOC_MAX_TRACKS = 32768
 NOALLOC_MAX_ITERS = 4096
 
 
+def _noalloc_check_tensor(name, t, dtype, min_elems):
+    """Refuse a device buffer the library would read or write out of bounds."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"et_transport_noalloc: {name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"et_transport_noalloc: {name} must be {dtype}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"et_transport_noalloc: {name} must be contiguous")
+    if t.numel() < min_elems:
+        raise ValueError(f"et_transport_noalloc: {name} holds {t.numel()} elements,"
+                         f" {min_elems} needed")
+
+
+def _noalloc_check_device(name, t, device):
+    if not t.is_cuda:
+        raise ValueError(f"et_transport_noalloc: {name} is not in device memory")
+    if device is not None and t.device != device:
+        raise ValueError(f"et_transport_noalloc: {name} is on {t.device}, not {device}")
+
+
 def et_transport_noalloc(geom, tables, primaries_device, n_primaries, seed, n_events,
                          score_device, ledger_device, stream=None):
-    """The allocation-free transport of one batch (see et.h).  primaries_device: CUDA
-    tensor (or address) of n_primaries 48-byte records; score_device: CUDA float64
-    [n_events][n_slabs]; ledger_device: CUDA float64 [n_events][5].  Returns the steps."""
+    """The allocation-free transport of one batch (see et.h).  primaries_device: CUDA uint8
+    tensor holding n_primaries 48-byte records; score_device: CUDA float64
+    [n_events][n_slabs]; ledger_device: CUDA float64 [n_events][5], both on the primaries'
+    device.  Every buffer is checked (type, device, contiguity, size) before the library
+    is called, since the kernels write score[event][slab] and ledger[event][k] for every
+    event below n_events.  Returns the steps."""
     import torch
     th = np.ascontiguousarray(geom["thickness"], dtype=np.float64)
     mat = np.ascontiguousarray(geom["material"], dtype=np.uint8)
     sig = np.ascontiguousarray(tables["sigma"], dtype=np.float32)
     dedx = np.ascontiguousarray(tables["dedx"], dtype=np.float32)
-    addr = lambda x: x if isinstance(x, int) else x.data_ptr()
+    if sig.ndim != 3 or sig.shape[1:] != (N_TAB, N_NODES):
+        raise ValueError(f"et_transport_noalloc: sigma must be [n_materials][{N_TAB}]"
+                         f"[{N_NODES}], not {list(sig.shape)}")
+    if dedx.shape != (sig.shape[0],):
+        raise ValueError("et_transport_noalloc: dedx must hold one value per material")
+    if len(mat) != len(th):
+        raise ValueError("et_transport_noalloc: thickness and material differ in length")
+    n_primaries, n_events = int(n_primaries), int(n_events)
+    if n_primaries < 0 or n_events < 1:
+        raise ValueError("et_transport_noalloc: n_primaries >= 0 and n_events >= 1 needed")
+    if not 0 <= int(seed) < (1 << 32):
+        raise ValueError("et_transport_noalloc: the seed keys Philox with 32 bits")
+    _noalloc_check_tensor("primaries_device", primaries_device, torch.uint8,
+                          n_primaries * PRIMARY_DTYPE.itemsize)
+    _noalloc_check_tensor("score_device", score_device, torch.float64, n_events * len(th))
+    _noalloc_check_tensor("ledger_device", ledger_device, torch.float64, n_events * 5)
+    dev = primaries_device.device
+    for name, t in (("primaries_device", primaries_device), ("score_device", score_device),
+                    ("ledger_device", ledger_device)):
+        _noalloc_check_device(name, t, dev)
     if stream is None:
-        s = torch.cuda.current_stream().cuda_stream
+        s = torch.cuda.current_stream(dev).cuda_stream
     else:
         s = stream if isinstance(stream, int) else stream.cuda_stream
     steps = C.c_uint64()
     err = C.create_string_buffer(256)
-    st = lib.et_transport_noalloc(len(th), _p(th), _p(mat), float(geom["half_xy"]), sig.shape[0],
-                                  float(tables["log_emin"]), float(tables["inv_dlog"]), _p(sig),
-                                  _p(dedx), C.c_void_p(addr(primaries_device)), n_primaries, seed,
-                                  n_events, C.c_void_p(addr(score_device)),
-                                  C.c_void_p(addr(ledger_device)), C.byref(steps), C.c_void_p(s),
-                                  err, len(err))
+    with torch.cuda.device(dev):
+        st = lib.et_transport_noalloc(len(th), _p(th), _p(mat), float(geom["half_xy"]),
+                                      sig.shape[0], float(tables["log_emin"]),
+                                      float(tables["inv_dlog"]), _p(sig), _p(dedx),
+                                      C.c_void_p(primaries_device.data_ptr()), n_primaries,
+                                      int(seed), n_events, C.c_void_p(score_device.data_ptr()),
+                                      C.c_void_p(ledger_device.data_ptr()), C.byref(steps),
+                                      C.c_void_p(s), err, len(err))
     if st != ET_OK:
         raise EtError(st, err.value.decode())
     return steps.value

@@ -46,3 +46,19 @@ def test_autotuned_batched_run_matches_oracle(geom):
     g = run_gpu(geom, p, 24, form="dense", layout=b["layout"], driver=b["driver"],
                 block_size=b["block_size"], capacity_log2=18)
     assert_strict_parity(g, oracle_run(geom, p, 24))
+
+
+def test_tuned_record_round_trip(tmp_path):
+    from paper_2302_08252_gb300 import tuned
+    path = str(tmp_path / "tuned.json")
+    best = {"form": "dense", "layout": "aosoa64", "block_size": 256, "driver": "hybrid",
+            "seconds": 0.1}
+    tuned.write("uneven", best, "a sample", "cmd", path=path)
+    tuned.write("mixed", dict(best, layout="aosoa32"), "a sample", "cmd", path=path)
+    assert tuned.config("uneven", path=path) == {k: best[k] for k in tuned.KEYS}
+    assert tuned.config("mixed", path=path)["layout"] == "aosoa32"
+    assert tuned.config("jittered", path=path) is None
+    # the committed record names a configuration the library accepts
+    c = tuned.config("uneven")
+    assert c["layout"] in autotune.LAYOUTS and c["driver"] in autotune.DRIVERS
+    assert c["block_size"] in autotune.BLOCKS and c["form"] in ("dense", "sparse")

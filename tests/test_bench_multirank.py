@@ -6,6 +6,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -70,16 +71,39 @@ def test_reference_arm_runs_on_rank_zero_only():
 
 
 @pytest.mark.parametrize("argv,workload,driver,cap", [
-    ([], "jittered", "persistent", 22),
+    ([], "uneven", None, 26),
+    (["--config", "2"], "jittered", "persistent", 22),
     (["--config", "1"], "small", "persistent", 16),
     (["--config", "3"], "mixed", "hybrid", 24),
-    (["--config", "4"], "uneven", "hybrid", 26),
+    (["--config", "4"], "uneven", None, 26),
     (["--config", "4", "--driver", "graph", "--capacity-log2", "25"], "uneven", "graph", 25),
 ])
 def test_bench_workload_defaults(argv, workload, driver, cap):
-    """Configuration numbers pick the workload; the driver and capacity default per
-    workload (the fastest measured driver) unless given."""
+    """Configuration numbers pick the workload (the batched events by default); layout,
+    block size and driver default to the autotuner's pick for the workload where it has
+    one (None above), else to the fastest measured driver; capacity per workload."""
     sys.path.insert(0, ROOT)
     import bench
+    from paper_2302_08252_gb300 import tuned
     a = bench.parse_args(argv)
+    t = tuned.config(workload)
+    if driver is None:
+        driver = t["driver"]
+        assert (a.layout, a.block_size, a.form) == (t["layout"], t["block_size"], t["form"])
     assert (a.workload, a.driver, a.capacity_log2) == (workload, driver, cap)
+
+
+def test_oracle_samples_are_bounded():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2302_08252_gb300 import workloads as W
+    p = W.uneven_events(256, 1000)
+    s, what = bench.oracle_sample("uneven", p, 256, reference=True)
+    assert len(s) == (len(p) + 31) // 32 and "one primary in 32" in what
+    assert np.array_equal(s["id"], p["id"][::32]) and np.array_equal(s["event"], p["event"][::32])
+    s, _ = bench.oracle_sample("uneven", p, 256, reference=False)
+    assert len(s) == (len(p) + 3) // 4
+    q = W.jittered_electrons()
+    s, what = bench.oracle_sample("jittered", q, 1000, reference=True)
+    assert len(s) == 100 and what == "first 100 events"
+    assert len(bench.oracle_sample("jittered", q, 1000, reference=False)[0]) == 1000

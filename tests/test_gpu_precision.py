@@ -6,10 +6,15 @@ Runs the same primaries through
   fp64     the all-FP64 GPU build
   oracle64 the FP64 reference oracle (CPU, all cores)
   oracle32 the strict FP32 oracle (CPU, all cores; the bit-exact target of fp32)
-and prints one JSON object with, per layer (absorber + gap summed), the mean deposit per
-primary and its standard error, each result's error against oracle64, and the run times.
+and computes, per layer (absorber + gap summed), the mean deposit per primary and its
+standard error, each result's error against oracle64, and the run times.  As a test it
+asserts the precision claims on the whole workload: fp32 bit-exact with oracle32 (steps
+and per-iteration counts; deposits to 1e-6), fp64 on oracle64's histories (steps and
+iterations), and fp32's and fp64's per-layer means within 3 standard errors and 1 % of
+oracle64's on the layers holding at least 1 % of the deposit.  Run as a script it prints
+the report as one JSON object:
 
-    python tests/precision_report.py [--n 10000] [--out FILE]
+    python tests/test_gpu_precision.py [--n 10000] [--out FILE]
 """
 import argparse
 import json
@@ -24,13 +29,10 @@ sys.path.insert(0, os.path.dirname(HERE))
 sys.path.insert(0, HERE)
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, default=10000)
-    ap.add_argument("--out", default=None)
-    ap.add_argument("--capacity-log2", type=int, default=24)
-    a = ap.parse_args()
+import pytest
 
+
+def precision_report(n=10000, capacity_log2=24):
     import torch
 
     import oracle
@@ -39,7 +41,6 @@ def main():
     from parity import run_gpu
 
     geom = W.calorimeter()
-    n = a.n
     p = W.mixed_primaries(n)
     e_in = p["ekin"].astype(np.float64)
     res = {"workload": f"{n} mixed primaries (50% e-, 25% e+, 25% gamma), 0.1-100 GeV "
@@ -47,12 +48,12 @@ def main():
 
     t = time.perf_counter()
     g = run_gpu(geom, p, n, form="dense", layout="aosoa32", driver="persistent", mode=0,
-                id_log=False, capacity_log2=a.capacity_log2)
+                id_log=False, capacity_log2=capacity_log2)
     torch.cuda.synchronize()
     res["runs"]["fp32"] = {"seconds": time.perf_counter() - t, "steps": int(sum(g["counters"]["steps"]))}
     t = time.perf_counter()
     s64, l64, steps64, it64 = et.et_run_fp64(geom, et.et_build_toy_tables_fp64(), p, 1, n,
-                                             a.capacity_log2)
+                                             capacity_log2)
     res["runs"]["fp64"] = {"seconds": time.perf_counter() - t, "steps": int(steps64)}
     nth = os.cpu_count() or 1
     t = time.perf_counter()
@@ -94,7 +95,30 @@ def main():
     }
     res["fp64_vs_oracle64"] = {"steps_equal": int(steps64) == int(o64["steps"].sum()),
                                "iterations": [int(it64), int(o64["n_iters"])]}
-    line = json.dumps(res)
+    return res
+
+
+@pytest.mark.gpu
+def test_precision_mixed_primaries():
+    r = precision_report()
+    assert r["fp32_vs_oracle32"]["steps_equal"] and r["fp32_vs_oracle32"]["counts_equal"]
+    assert r["fp32_vs_oracle32"]["deposit_rel_err_max"] <= 1e-6
+    assert r["fp64_vs_oracle64"]["steps_equal"]
+    it = r["fp64_vs_oracle64"]["iterations"]
+    assert it[0] == it[1]
+    for name in ("fp32", "fp64", "oracle32"):
+        assert r[name]["layer_err_in_se_max"] <= 3.0, name
+        assert r[name]["layer_rel_err_max_big_layers"] <= 0.01, name
+    assert r["fp64"]["per_event_slab_abs_err_over_e_max"] <= 1e-9
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=10000)
+    ap.add_argument("--out", default=None)
+    ap.add_argument("--capacity-log2", type=int, default=24)
+    a = ap.parse_args()
+    line = json.dumps(precision_report(a.n, a.capacity_log2))
     print(line)
     if a.out:
         with open(a.out, "w") as f:

@@ -147,3 +147,38 @@ def test_layout_mappings_tile_the_buffer(layout):
             assert a % size == 0 and 0 <= a and a + size <= cap * 64
             used[a:a + size] += 1
     assert np.all(used == 1)
+
+
+def test_noalloc_wrapper_refuses_bad_buffers(libet, geom):
+    # every refusal happens on the host, before the library is called
+    import torch
+
+    from paper_2302_08252_gb300 import et
+    from paper_2302_08252_gb300 import workloads as W
+    tables = et.et_build_toy_tables()
+    n_slabs, n_ev = len(geom["thickness"]), 4
+    prim = torch.zeros(3 * 48, dtype=torch.uint8)
+    score = torch.zeros((n_ev, n_slabs), dtype=torch.float64)
+    ledger = torch.zeros((n_ev, 5), dtype=torch.float64)
+
+    def call(t=tables, p=prim, n=3, seed=1, ev=n_ev, s=score, lg=ledger):
+        return et.et_transport_noalloc(geom, t, p, n, seed, ev, s, lg)
+
+    cases = [
+        (dict(t=dict(tables, sigma=tables["sigma"][:, :, :256])), "sigma"),
+        (dict(t=dict(tables, dedx=tables["dedx"][:1])), "dedx"),
+        (dict(seed=1 << 32), "seed"),
+        (dict(ev=0), "n_events"),
+        (dict(p=np.zeros(3 * 48, np.uint8)), "primaries_device must be a CUDA tensor"),
+        (dict(p=torch.zeros(3 * 48, dtype=torch.int8)), "primaries_device must be torch.uint8"),
+        (dict(n=4), "primaries_device holds 144"),
+        (dict(s=torch.zeros((n_ev, n_slabs), dtype=torch.float32)), "score_device must be"),
+        (dict(s=torch.zeros((n_ev - 1, n_slabs), dtype=torch.float64)), "score_device holds"),
+        (dict(s=torch.zeros((n_slabs, 2 * n_ev), dtype=torch.float64).t()), "contiguous"),
+        (dict(lg=torch.zeros((n_ev, 4), dtype=torch.float64)), "ledger_device holds"),
+        ({}, "primaries_device is not in device memory"),
+    ]
+    for kw, msg in cases:
+        with pytest.raises((TypeError, ValueError), match=msg):
+            call(**kw)
+    assert W.PRIMARY_DTYPE.itemsize == 48

@@ -1,49 +1,86 @@
-"""The allocation-free entry point (et_transport_noalloc) against the regular one.
+"""The allocation-free entry point (et_transport_noalloc), through the C ABI.
 
 For callers that cannot allocate device memory (inside another framework's memory pool,
 under an allocation budget, or where cudaMalloc's implicit synchronisation is not
 allowed), the library offers one call whose scratch lives in a fixed device array.  This
-file checks, through the C ABI, that two calls in a row give the deposits, ledger and step
-count of the context-based path (strict mode; deposits within the parity tolerance), and
-that oversize requests are refused with a clear error.  It is named to be collected last.
+file checks that two calls in a row give the oracle's step count, deposits and ledger and
+the context-based path's results (strict mode; deposits within the parity tolerance), on
+16 electrons of 1 GeV and on a batch of mixed types; that the second call takes no device
+memory; that oversize batches, an overflowing shower and an invalid primary are refused
+with a clear error; and that a call after a refused one starts clean (the scratch array
+is shared by every call).  It is named to be collected last.
 """
 import numpy as np
 import pytest
 
 from paper_2302_08252_gb300 import workloads as W
 
-from parity import DEPOSIT_RTOL, run_gpu
+from parity import DEPOSIT_RTOL, oracle_run, run_gpu
 
 pytestmark = pytest.mark.gpu
+
+# oracle ledger columns: injected, deposited_cont, below_cut, escaped, mass_created,
+# mass_consumed; the entry point's: injected, below_cut, escaped, mass_created,
+# mass_consumed
+LEDGER_COLS = ((0, 0), (1, 2), (2, 3), (3, 4), (4, 5))
 
 
 def _close(a, b):
     return np.all(np.abs(a - b) <= DEPOSIT_RTOL * np.abs(b) + 1e-9)
 
 
-def test_noalloc_matches_the_context_path_on_two_calls(geom):
+def _mixed_small():
+    """Mixed e-/e+/gamma primaries below 3 GeV from the mixed generator (205 primaries in
+    events numbered up to 399): every type's peak population stays inside the fixed
+    scratch (oracle peaks 5,501 / 1,614 / 14,431)."""
+    p = W.mixed_primaries(400)
+    return p[p["ekin"] < 3000.0], 400
+
+
+def _buffers(n_events, n_slabs):
+    import torch
+    score = torch.full((n_events, n_slabs), 7.0, dtype=torch.float64, device="cuda")
+    ledger = torch.full((n_events, 5), 7.0, dtype=torch.float64, device="cuda")
+    return score, ledger
+
+
+def _check_against(ref_steps, ref_score, ref_ledger, steps, score, ledger):
+    assert steps == ref_steps
+    s = score.cpu().numpy()
+    lg = ledger.cpu().numpy()
+    assert _close(s, ref_score)
+    assert np.array_equal(lg[:, 0], ref_ledger[:, 0])
+    for mine, theirs in LEDGER_COLS[1:]:
+        assert _close(lg[:, mine], ref_ledger[:, theirs])
+
+
+@pytest.mark.parametrize("case", ["electrons_1GeV", "mixed_types"])
+def test_noalloc_matches_oracle_and_context_path_on_two_calls(geom, case):
     import torch
 
     from paper_2302_08252_gb300 import et
-    p = W.small_electrons()
-    n_events, n_slabs = 16, len(geom["thickness"])
-    ref = run_gpu(geom, p, n_events, form="dense", layout="aos", driver="persistent", id_log=False)
-    ref_steps = sum(ref["counters"]["steps"])
+    if case == "electrons_1GeV":
+        p, n_events = W.small_electrons(), 16
+    else:
+        p, n_events = _mixed_small()
+    n_slabs = len(geom["thickness"])
+    o = oracle_run(geom, p, n_events, idlog=False, nthreads=16)
+    assert int(o["counts"].max()) <= et.NOALLOC_MAX_TRACKS
+    ref = run_gpu(geom, p, n_events, form="dense", layout="aos", driver="persistent",
+                  id_log=False)
     tables = et.et_build_toy_tables()
     d_prim = torch.from_numpy(p.view(np.uint8).copy()).cuda()
-    score = torch.full((n_events, n_slabs), 7.0, dtype=torch.float64, device="cuda")
-    ledger = torch.full((n_events, 5), 7.0, dtype=torch.float64, device="cuda")
-    for _ in range(2):
+    score, ledger = _buffers(n_events, n_slabs)
+    for call in range(2):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         steps = et.et_transport_noalloc(geom, tables, d_prim, len(p), 1, n_events, score, ledger)
         torch.cuda.synchronize()
-        assert steps == ref_steps
-        s = score.cpu().numpy()
-        lg = ledger.cpu().numpy()
-        assert _close(s, ref["score"])
-        rl = ref["ledger"]  # injected, deposited_cont, below_cut, escaped, mass_created, mass_consumed
-        assert np.array_equal(lg[:, 0], rl[:, 0])
-        for mine, theirs in ((1, 2), (2, 3), (3, 4), (4, 5)):
-            assert _close(lg[:, mine], rl[:, theirs])
+        if call:  # the first call may load the library's modules; the second takes nothing
+            assert torch.cuda.mem_get_info()[0] == free0
+        _check_against(int(o["steps"].sum()), o["score"], o["ledger"], steps, score, ledger)
+        _check_against(sum(ref["counters"]["steps"]), ref["score"], ref["ledger"], steps,
+                       score, ledger)
 
 
 def test_noalloc_refuses_oversize_batches(geom):
@@ -54,9 +91,40 @@ def test_noalloc_refuses_oversize_batches(geom):
     n = et.NOALLOC_MAX_TRACKS + 1
     p = W.gun(n, 1.0, ptype=W.GAMMA)
     d_prim = torch.from_numpy(p.view(np.uint8).copy()).cuda()
-    score = torch.zeros((n, len(geom["thickness"])), dtype=torch.float64, device="cuda")
-    ledger = torch.zeros((n, 5), dtype=torch.float64, device="cuda")
+    score, ledger = _buffers(n, len(geom["thickness"]))
     with pytest.raises(et.EtError) as e:
         et.et_transport_noalloc(geom, tables, d_prim, n, 1, n, score, ledger)
     assert e.value.status == et.ET_ERR_CAPACITY
     assert "ET_NOALLOC_MAX_TRACKS" in str(e.value)
+
+
+def test_noalloc_refusals_then_a_clean_call(geom):
+    import torch
+
+    from paper_2302_08252_gb300 import et
+    tables = et.et_build_toy_tables()
+    n_slabs = len(geom["thickness"])
+    # 4,000 photons of 10 GeV: a legal primary count whose showers outgrow the fixed
+    # scratch (the oracle's photon peak is 3.2 M tracks), refused by the device-side
+    # capacity guard
+    big = W.gun(4000, 10000.0, ptype=W.GAMMA)
+    d_big = torch.from_numpy(big.view(np.uint8).copy()).cuda()
+    score, ledger = _buffers(4000, n_slabs)
+    with pytest.raises(et.EtError) as e:
+        et.et_transport_noalloc(geom, tables, d_big, len(big), 1, 4000, score, ledger)
+    assert e.value.status == et.ET_ERR_CAPACITY
+    # one primary numbered past the last event: skipped on the device, reported invalid
+    p = W.small_electrons()
+    bad = p.copy()
+    bad["event"][3] = 16
+    d_bad = torch.from_numpy(bad.view(np.uint8).copy()).cuda()
+    score, ledger = _buffers(16, n_slabs)
+    with pytest.raises(et.EtError) as e:
+        et.et_transport_noalloc(geom, tables, d_bad, len(bad), 1, 16, score, ledger)
+    assert e.value.status == et.ET_ERR_INVALID
+    # the next call starts from a clean control block and matches the oracle
+    o = oracle_run(geom, p, 16, idlog=False)
+    d_prim = torch.from_numpy(p.view(np.uint8).copy()).cuda()
+    steps = et.et_transport_noalloc(geom, tables, d_prim, len(p), 1, 16, score, ledger)
+    torch.cuda.synchronize()
+    _check_against(int(o["steps"].sum()), o["score"], o["ledger"], steps, score, ledger)
