@@ -474,11 +474,12 @@ def ours_arm(args, rank, world, group):
     }
 
     barrier(group)
-    e2e_steps, e2e_secs, h2d, d2h = e2e_measure(et, tuned["ctx"], prim, n_events, n_slabs,
-                                                args.e2e_steps)
-    e2e_all, e2e_max = aggregate(float(e2e_steps), e2e_secs, group)
-    line["e2e"] = {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h}
+    if args.e2e_steps > 0:
+        e2e_steps, e2e_secs, h2d, d2h = e2e_measure(et, tuned["ctx"], prim, n_events, n_slabs,
+                                                    args.e2e_steps)
+        e2e_all, e2e_max = aggregate(float(e2e_steps), e2e_secs, group)
+        line["e2e"] = {"value": e2e_all / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h}
     if rank == 0 and world == 1:
         if not args.no_plain:
             # the large workloads create more tracks than a sparse buffer without reuse
