@@ -25,7 +25,7 @@ N_NODES = 257
 N_MAT = 2
 N_TAB = 5
 TAB_COMPTON, TAB_PAIR, TAB_PHOT, TAB_TOT, TAB_BREM = range(5)
-LIM_Z, LIM_X, LIM_Y, LIM_LOSS, LIM_PHYS = range(5)
+LIM_Z, LIM_X, LIM_Y, LIM_LOSS, LIM_PHYS, LIM_MSC = range(6)
 PROC_NONE, PROC_COMPTON, PROC_PAIR, PROC_PHOT, PROC_BREM = range(5)
 ALIVE, DEATH_ESCAPE, DEATH_CUT, DEATH_ABSORB = range(4)
 LEDGER_FIELDS = ("injected", "deposited_cont", "below_cut", "escaped", "mass_created",
@@ -60,7 +60,8 @@ class _World(C.Structure):
                 ("half_xy", C.c_float), ("log_emin32", C.c_float), ("inv_dlog32", C.c_float),
                 ("pad1", C.c_float), ("log_emin64", C.c_double), ("inv_dlog64", C.c_double),
                 ("sig32", C.c_void_p), ("sig64", C.c_void_p), ("dedx32", C.c_void_p),
-                ("dedx64", C.c_void_p), ("seed", C.c_uint64)]
+                ("dedx64", C.c_void_p), ("seed", C.c_uint64), ("msc", C.c_int32),
+                ("pad2", C.c_int32), ("x0_32", C.c_void_p), ("x0_64", C.c_void_p)]
 
 
 class _Totals(C.Structure):
@@ -94,6 +95,8 @@ def lib():
             getattr(L, n).restype = C.c_double
         L.oracle_dedx.argtypes = [C.c_int]
         L.oracle_dedx.restype = C.c_double
+        L.oracle_x0.argtypes = [C.c_int]
+        L.oracle_x0.restype = C.c_double
         L.oracle_kn_per_electron_cm2.argtypes = [C.c_double]
         L.oracle_kn_per_electron_cm2.restype = C.c_double
         L.oracle_electron_density_cm3.argtypes = [C.c_int]
@@ -194,10 +197,16 @@ def build_tables(n_nodes: int = N_NODES, n_mat: int = N_MAT) -> dict:
             "n_mat": n_mat}
 
 
-class World:
-    """Geometry + tables + seed, kept alive for the C side."""
+def radiation_lengths(n_mat: int = N_MAT) -> np.ndarray:
+    """Radiation length X0 (mm) per material (FP64)."""
+    return np.array([lib().oracle_x0(m) for m in range(n_mat)], dtype=np.float64)
 
-    def __init__(self, geom: dict, tables: dict | None = None, seed: int = 1):
+
+class World:
+    """Geometry + tables + seed, kept alive for the C side.  msc=True selects the toy
+    model v2 (multiple scattering of e+-) with the materials' radiation lengths."""
+
+    def __init__(self, geom: dict, tables: dict | None = None, seed: int = 1, msc: bool = False):
         self.tables = tables if tables is not None else build_tables()
         t = self.tables
         self._keep = [np.ascontiguousarray(geom["thickness"], np.float64),
@@ -223,15 +232,22 @@ class World:
         w.dedx32 = d32.ctypes.data
         w.dedx64 = d64.ctypes.data
         w.seed = int(seed)
+        x0 = radiation_lengths(int(t["n_mat"]))
+        self._keep += [x0.astype(np.float32), x0]
+        w.msc = int(bool(msc))
+        w.x0_32 = self._keep[-2].ctypes.data
+        w.x0_64 = self._keep[-1].ctypes.data
         self.c = w
         self.n_slabs = len(th)
 
 
 def run(geom: dict, primaries: np.ndarray, n_events: int | None = None, seed: int = 1,
         mode: int = STRICT_FP32, nthreads: int = 1, max_iters: int = 1 << 16,
-        idlog: bool = False, tables: dict | None = None, world: World | None = None) -> dict:
-    """Run primaries (workloads.PRIMARY_DTYPE) to completion; returns numpy results."""
-    w = world if world is not None else World(geom, tables, seed)
+        idlog: bool = False, tables: dict | None = None, world: World | None = None,
+        msc: bool = False) -> dict:
+    """Run primaries (workloads.PRIMARY_DTYPE) to completion; returns numpy results.
+    msc=True runs the toy model v2 (multiple scattering)."""
+    w = world if world is not None else World(geom, tables, seed, msc=msc)
     prim = np.ascontiguousarray(primaries)
     assert prim.dtype.itemsize == 48
     if n_events is None:

@@ -23,7 +23,9 @@
  * Parity pins (tests/test_oracle_*.py): Philox known-answer vectors, spec-math
  * error against libm, tables against numerically integrated cross sections,
  * Klein-Nishina chi-square, bremsstrahlung KS, exponential attenuation,
- * range closed form, single-interaction kinematics, energy ledger closure.
+ * range closed form, single-interaction kinematics, energy ledger closure, and
+ * for the toy model v2 (multiple scattering) the step limit's closed form and
+ * the deflection against Highland's width.
  */
 #ifndef ET_ORACLE_H
 #define ET_ORACLE_H
@@ -38,7 +40,7 @@ extern "C" {
 enum { OR_EM = 0, OR_EP = 1, OR_GAMMA = 2, OR_NTYPES = 3 };
 enum { OR_TAB_COMPTON = 0, OR_TAB_PAIR = 1, OR_TAB_PHOT = 2, OR_TAB_TOT = 3, OR_TAB_BREM = 4,
        OR_NTAB = 5 };
-enum { OR_LIM_Z = 0, OR_LIM_X = 1, OR_LIM_Y = 2, OR_LIM_LOSS = 3, OR_LIM_PHYS = 4 };
+enum { OR_LIM_Z = 0, OR_LIM_X = 1, OR_LIM_Y = 2, OR_LIM_LOSS = 3, OR_LIM_PHYS = 4, OR_LIM_MSC = 5 };
 enum { OR_PROC_NONE = 0, OR_PROC_COMPTON = 1, OR_PROC_PAIR = 2, OR_PROC_PHOT = 3,
        OR_PROC_BREM = 4 };
 enum { OR_ALIVE = 0, OR_DEATH_ESCAPE = 1, OR_DEATH_CUT = 2, OR_DEATH_ABSORB = 3 };
@@ -106,6 +108,7 @@ double oracle_sigma_pair(int mat, double e_mev);
 double oracle_sigma_phot(int mat, double e_mev);
 double oracle_sigma_brem(int mat, double t_mev);
 double oracle_dedx(int mat);
+double oracle_x0(int mat);   /* radiation length, mm */
 double oracle_kn_per_electron_cm2(double k);
 double oracle_electron_density_cm3(int mat);
 
@@ -132,6 +135,10 @@ typedef struct {
   const float* dedx32;       /* [n_mat] MeV/mm */
   const double* dedx64;
   uint64_t seed;
+  int32_t msc;               /* 0: toy model v1; 1: v2, with multiple scattering */
+  int32_t pad2;
+  const float* x0_32;        /* [n_mat] radiation lengths, mm (v2 only) */
+  const double* x0_64;
 } oracle_world;
 
 typedef struct {

@@ -73,6 +73,8 @@ double oracle_sigma_brem(int mat, double t) {
 
 double oracle_dedx(int mat) { return OR_MATS[mat].dedx; }
 
+double oracle_x0(int mat) { return OR_MATS[mat].X0_mm; }
+
 int oracle_build_tables(int n_mat, int n_nodes, float* sig32, double* sig64, float* dedx32,
                         double* dedx64, float* log_emin32, float* inv_dlog32, double* log_emin64,
                         double* inv_dlog64) {

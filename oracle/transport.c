@@ -63,6 +63,7 @@ static void or_worker_idlog(or_worker* wk, uint64_t id, uint32_t steps, uint32_t
 #define R_LOGEMIN(w) ((w)->log_emin32)
 #define R_INVDLOG(w) ((w)->inv_dlog32)
 #define R_DEDX(w) ((w)->dedx32)
+#define R_X0(w) ((w)->x0_32)
 #include "transport_body.h"
 #undef REAL
 #undef SFX
@@ -77,6 +78,7 @@ static void or_worker_idlog(or_worker* wk, uint64_t id, uint32_t steps, uint32_t
 #undef R_LOGEMIN
 #undef R_INVDLOG
 #undef R_DEDX
+#undef R_X0
 
 /* ---- FP64 reference instantiation ---- */
 static void or_sincos2pi64(double u, double* s, double* c) {
@@ -97,6 +99,7 @@ static void or_sincos2pi64(double u, double* s, double* c) {
 #define R_LOGEMIN(w) ((w)->log_emin64)
 #define R_INVDLOG(w) ((w)->inv_dlog64)
 #define R_DEDX(w) ((w)->dedx64)
+#define R_X0(w) ((w)->x0_64)
 #include "transport_body.h"
 
 /* ------------------------------------------------------------------ */

@@ -5,7 +5,7 @@
  * polynomials for log/exp/sincos, FP32 tables) and once as the FP64 reference
  * (libm, FP64 tables).  Macros supplied by the includer:
  *   REAL, SFX(name), RC(literal), R_LOG, R_EXP, R_SQRT, R_FLOOR, R_SINCOS2PI,
- *   R_INF, R_SIG (table pointer in the world), R_LOGEMIN, R_INVDLOG, R_DEDX.
+ *   R_INF, R_SIG (table pointer in the world), R_LOGEMIN, R_INVDLOG, R_DEDX, R_X0.
  *
  * One call of SFX(step) is one step of one track: Sec. 2 of the paper (each
  * active track is advanced once per transport iteration; survivors and
@@ -43,7 +43,14 @@ typedef struct {
   REAL log_emin, inv_dlog;
   const REAL* sig; /* [n_mat][5][n_nodes] */
   REAL dedx[4];
+  int msc;         /* toy model v2: multiple scattering of e+- */
+  REAL x0[4];      /* radiation lengths (mm), v2 only */
 } SFX(env);
+
+/* Toy model v2: the multiple-scattering step limit is OR_MSC_FR times the larger of the
+ * range E / dEdx and OR_MSC_RMIN (mm). */
+#define OR_MSC_FR RC(0.04)
+#define OR_MSC_RMIN RC(0.5)
 
 static int SFX(env_init)(SFX(env) * v, const oracle_world* w) {
   if (w->n_slabs < 1 || w->n_slabs > 128 || w->n_mat < 1 || w->n_mat > 4 || w->n_nodes < 2)
@@ -64,6 +71,15 @@ static int SFX(env_init)(SFX(env) * v, const oracle_world* w) {
   v->inv_dlog = R_INVDLOG(w);
   v->sig = R_SIG(w);
   for (int m = 0; m < w->n_mat; ++m) v->dedx[m] = R_DEDX(w)[m];
+  v->msc = w->msc != 0;
+  for (int m = 0; m < 4; ++m) v->x0[m] = RC(0.0);
+  if (v->msc) {
+    if (!R_X0(w)) return 1;
+    for (int m = 0; m < w->n_mat; ++m) {
+      v->x0[m] = R_X0(w)[m];
+      if (!(v->x0[m] > RC(0.0))) return 1;
+    }
+  }
   return 0;
 }
 
@@ -129,6 +145,34 @@ static void SFX(annihilate)(const SFX(env) * v, const SFX(trk) * t, uint32_t pst
   SFX(add_sec)(o, t, pstep, OR_GAMMA, RC(0.51099895), dx, dy, dz);
   SFX(add_sec)(o, t, pstep, OR_GAMMA, RC(0.51099895), -dx, -dy, -dz);
   o->mcr = (double)RC(0.51099895) + (double)RC(0.51099895);
+}
+
+/* Toy model v2, multiple scattering: the direction of a charged track that goes on after
+ * a step of length s > 0 in material m is turned by a polar angle theta and an azimuth
+ * phi (Philox block 66 of the step).  The width is the Highland formula of the pre-step
+ * energy E, theta0 = 13.6 MeV / (beta c p) sqrt(x) (1 + 0.038 ln x), x = s / X0 (no
+ * deflection when the bracket is not positive); beta c p = E (E + 2 mc^2) / (E + mc^2).
+ * In the small-angle Gaussian approximation theta^2 / 2 is exponential with mean
+ * theta0^2, so 1 - cos(theta) = theta0^2 (-ln u0), cos(theta) clamped at -1; phi = 2 pi u1.
+ * The turn uses the same rotation as the Compton scattering. */
+static void SFX(msc_deflect)(const SFX(env) * v, SFX(trk) * t, uint32_t pstep, REAL E, REAL s,
+                             int m) {
+  REAL pbc = E * (E + RC(1.0219979)) / (E + RC(0.51099895));
+  REAL x = s / v->x0[m];
+  REAL br = RC(1.0) + RC(0.038) * R_LOG(x);
+  if (!(br > RC(0.0))) return;
+  REAL th0 = (RC(13.6) / pbc) * R_SQRT(x) * br;
+  REAL u[4];
+  SFX(draws)(v->seed, t->event, t->id, pstep, 66u, u);
+  REAL w = (th0 * th0) * (-R_LOG(u[0]));
+  REAL cost = RC(1.0) - w;
+  if (cost < RC(-1.0)) cost = RC(-1.0);
+  REAL sint = R_SQRT((RC(1.0) - cost) * (RC(1.0) + cost));
+  REAL sp, cp;
+  R_SINCOS2PI(u[1], &sp, &cp);
+  REAL n[3];
+  SFX(rotate)(t->dx, t->dy, t->dz, sint * cp, sint * sp, cost, n);
+  t->dx = n[0]; t->dy = n[1]; t->dz = n[2];
 }
 
 /* Butcher-Messel Klein-Nishina sampling of eps = E'/E at k = E/mc^2; attempt j uses
@@ -210,6 +254,13 @@ static void SFX(step)(const SFX(env) * v, int type, SFX(trk) * t, SFX(out) * o) 
     REAL dedx = v->dedx[m];
     REAL sl = (E > RC(1.0)) ? (RC(0.2) * E) / dedx : E / dedx;
     if (sl < s) { s = sl; lim = OR_LIM_LOSS; }
+    if (v->msc) {
+      /* v2: multiple-scattering step limit, a fraction of the range E/dEdx (at least of
+       * the minimum range) */
+      REAL rng = E / dedx;
+      REAL sm = OR_MSC_FR * ((rng > OR_MSC_RMIN) ? rng : OR_MSC_RMIN);
+      if (sm < s) { s = sm; lim = OR_LIM_MSC; }
+    }
   }
   if (s_phys < s) { s = s_phys; lim = OR_LIM_PHYS; }
 
@@ -265,83 +316,87 @@ static void SFX(step)(const SFX(env) * v, int type, SFX(trk) * t, SFX(out) * o) 
     o->alive = 0;
     o->death = OR_DEATH_CUT;
     if (type == OR_EP) SFX(annihilate)(v, t, pstep, o);
-  } else if (lim == OR_LIM_PHYS) {
-    if (!charged) {
-      REAL sc = SFX(interp)(v, m, OR_TAB_COMPTON, i, f);
-      REAL sp = SFX(interp)(v, m, OR_TAB_PAIR, i, f);
-      REAL r = u[1] * sig;
-      if (r < sc) {
-        /* Compton */
-        o->proc = OR_PROC_COMPTON;
-        REAL k = E / RC(0.51099895);
-        REAL eps, onecost, sint2;
-        int j = SFX(compton_sample)(v->seed, t->event, t->id, pstep, k, &eps, &onecost, &sint2);
-        if (j >= 64) o->reject_cap_hit = 1;
-        if (sint2 < 0) sint2 = RC(0.0);
-        REAL cost = RC(1.0) - onecost;
-        REAL sint = R_SQRT(sint2);
-        REAL sphi, cphi;
-        R_SINCOS2PI(u[3], &sphi, &cphi);
-        REAL n[3];
-        SFX(rotate)(t->dx, t->dy, t->dz, sint * cphi, sint * sphi, cost, n);
-        REAL e1 = eps * E;
-        REAL te = E - e1;
-        if (te >= RC(0.01)) {
-          REAL px = E * t->dx - e1 * n[0];
-          REAL py = E * t->dy - e1 * n[1];
-          REAL pz = E * t->dz - e1 * n[2];
-          REAL pn = R_SQRT(px * px + py * py + pz * pz);
-          SFX(add_sec)(o, t, pstep, OR_EM, te, px / pn, py / pn, pz / pn);
-        } else {
-          o->cut = o->cut + (double)te;
-        }
-        t->dx = n[0]; t->dy = n[1]; t->dz = n[2];
-        t->e = e1;
-        if (!(e1 >= RC(0.01))) {
-          o->cut = o->cut + (double)e1;
+  } else {
+    /* v2: the surviving charged track is deflected before any interaction */
+    if (charged && v->msc && s > RC(0.0)) SFX(msc_deflect)(v, t, pstep, E, s, m);
+    if (lim == OR_LIM_PHYS) {
+      if (!charged) {
+        REAL sc = SFX(interp)(v, m, OR_TAB_COMPTON, i, f);
+        REAL sp = SFX(interp)(v, m, OR_TAB_PAIR, i, f);
+        REAL r = u[1] * sig;
+        if (r < sc) {
+          /* Compton */
+          o->proc = OR_PROC_COMPTON;
+          REAL k = E / RC(0.51099895);
+          REAL eps, onecost, sint2;
+          int j = SFX(compton_sample)(v->seed, t->event, t->id, pstep, k, &eps, &onecost, &sint2);
+          if (j >= 64) o->reject_cap_hit = 1;
+          if (sint2 < 0) sint2 = RC(0.0);
+          REAL cost = RC(1.0) - onecost;
+          REAL sint = R_SQRT(sint2);
+          REAL sphi, cphi;
+          R_SINCOS2PI(u[3], &sphi, &cphi);
+          REAL n[3];
+          SFX(rotate)(t->dx, t->dy, t->dz, sint * cphi, sint * sphi, cost, n);
+          REAL e1 = eps * E;
+          REAL te = E - e1;
+          if (te >= RC(0.01)) {
+            REAL px = E * t->dx - e1 * n[0];
+            REAL py = E * t->dy - e1 * n[1];
+            REAL pz = E * t->dz - e1 * n[2];
+            REAL pn = R_SQRT(px * px + py * py + pz * pz);
+            SFX(add_sec)(o, t, pstep, OR_EM, te, px / pn, py / pn, pz / pn);
+          } else {
+            o->cut = o->cut + (double)te;
+          }
+          t->dx = n[0]; t->dy = n[1]; t->dz = n[2];
+          t->e = e1;
+          if (!(e1 >= RC(0.01))) {
+            o->cut = o->cut + (double)e1;
+            o->alive = 0;
+            o->death = OR_DEATH_CUT;
+          }
+        } else if (r < sc + sp && E > RC(1.0219979)) {
+          /* pair: both leptons along the photon direction */
+          o->proc = OR_PROC_PAIR;
+          REAL avail = E - RC(1.0219979);
+          REAL em = u[2] * avail;
+          REAL ep = avail - em;
+          o->mc = ((double)E - (double)em) - (double)ep;
+          if (em >= RC(0.01)) SFX(add_sec)(o, t, pstep, OR_EM, em, t->dx, t->dy, t->dz);
+          else o->cut = o->cut + (double)em;
+          if (ep >= RC(0.01)) {
+            SFX(add_sec)(o, t, pstep, OR_EP, ep, t->dx, t->dy, t->dz);
+          } else {
+            o->cut = o->cut + (double)ep;
+            SFX(annihilate)(v, t, pstep, o);
+          }
           o->alive = 0;
-          o->death = OR_DEATH_CUT;
-        }
-      } else if (r < sc + sp && E > RC(1.0219979)) {
-        /* pair: both leptons along the photon direction */
-        o->proc = OR_PROC_PAIR;
-        REAL avail = E - RC(1.0219979);
-        REAL em = u[2] * avail;
-        REAL ep = avail - em;
-        o->mc = ((double)E - (double)em) - (double)ep;
-        if (em >= RC(0.01)) SFX(add_sec)(o, t, pstep, OR_EM, em, t->dx, t->dy, t->dz);
-        else o->cut = o->cut + (double)em;
-        if (ep >= RC(0.01)) {
-          SFX(add_sec)(o, t, pstep, OR_EP, ep, t->dx, t->dy, t->dz);
+          o->death = OR_DEATH_ABSORB;
         } else {
-          o->cut = o->cut + (double)ep;
-          SFX(annihilate)(v, t, pstep, o);
+          /* photoelectric: electron with the full energy along the photon direction */
+          o->proc = OR_PROC_PHOT;
+          if (E >= RC(0.01)) SFX(add_sec)(o, t, pstep, OR_EM, E, t->dx, t->dy, t->dz);
+          else o->cut = o->cut + (double)E;
+          o->alive = 0;
+          o->death = OR_DEATH_ABSORB;
         }
-        o->alive = 0;
-        o->death = OR_DEATH_ABSORB;
       } else {
-        /* photoelectric: electron with the full energy along the photon direction */
-        o->proc = OR_PROC_PHOT;
-        if (E >= RC(0.01)) SFX(add_sec)(o, t, pstep, OR_EM, E, t->dx, t->dy, t->dz);
-        else o->cut = o->cut + (double)E;
-        o->alive = 0;
-        o->death = OR_DEATH_ABSORB;
-      }
-    } else {
-      /* bremsstrahlung, 1/k spectrum on [k_c, T] */
-      o->proc = OR_PROC_BREM;
-      if (eout > RC(0.01)) {
-        REAL kk = RC(0.01) * R_EXP(u[2] * R_LOG(eout / RC(0.01)));
-        if (kk < RC(0.01)) kk = RC(0.01);
-        if (kk > eout) kk = eout;
-        SFX(add_sec)(o, t, pstep, OR_GAMMA, kk, t->dx, t->dy, t->dz);
-        REAL t2 = eout - kk;
-        t->e = t2;
-        if (t2 < RC(0.01)) {
-          o->cut = o->cut + (double)t2;
-          o->alive = 0;
-          o->death = OR_DEATH_CUT;
-          if (type == OR_EP) SFX(annihilate)(v, t, pstep, o);
+        /* bremsstrahlung, 1/k spectrum on [k_c, T] */
+        o->proc = OR_PROC_BREM;
+        if (eout > RC(0.01)) {
+          REAL kk = RC(0.01) * R_EXP(u[2] * R_LOG(eout / RC(0.01)));
+          if (kk < RC(0.01)) kk = RC(0.01);
+          if (kk > eout) kk = eout;
+          SFX(add_sec)(o, t, pstep, OR_GAMMA, kk, t->dx, t->dy, t->dz);
+          REAL t2 = eout - kk;
+          t->e = t2;
+          if (t2 < RC(0.01)) {
+            o->cut = o->cut + (double)t2;
+            o->alive = 0;
+            o->death = OR_DEATH_CUT;
+            if (type == OR_EP) SFX(annihilate)(v, t, pstep, o);
+          }
         }
       }
     }

@@ -208,6 +208,131 @@ def test_annihilation_angles_isotropic(oworld):
     assert stats.chi2_contingency(h)[1] > 1e-3
 
 
+# ---- toy model v2: multiple scattering of e+- ----
+
+MSC_FR, MSC_RMIN = 0.04, 0.5     # step limit: F_R max(E / dEdx, R_MIN), mm
+X0_PB, X0_LAR = 5.612, 140.0     # mm
+
+
+def highland_theta0(e_mev, s_mm, x0_mm):
+    """Highland's width of the projected scattering angle (PDG, Lynch and Dahl form):
+    13.6 MeV / (beta c p) sqrt(x) (1 + 0.038 ln x), x = s / X0, z = 1."""
+    pbc = e_mev * (e_mev + 2 * MC2) / (e_mev + MC2)  # (pc)^2 / E_total
+    x = s_mm / x0_mm
+    return 13.6 / pbc * np.sqrt(x) * (1.0 + 0.038 * np.log(x))
+
+
+@pytest.fixture(scope="module")
+def msc_world(otables):
+    return oracle.World(W.single_slab(5000.0, material=0), otables, seed=1, msc=True)
+
+
+@pytest.mark.parametrize("e", [0.1, 0.3, 1.0, 5.0, 50.0, 500.0])
+def test_msc_step_limit(msc_world, e):
+    # in a thick lead slab, with no interaction due, a charged step is limited by
+    # multiple scattering to F_R max(E / dEdx, R_MIN) (always below the loss limit)
+    for ptype in (W.E_MINUS, W.E_PLUS):
+        r = oracle.step_one(msc_world, ptype, oracle.make_track(z=0.0, e=e, nia=1e6, slab=0))
+        assert r["lim"] == oracle.LIM_MSC
+        rng = e / 1.274
+        assert float(r["track"]["len"]) == pytest.approx(MSC_FR * max(rng, MSC_RMIN), rel=1e-6)
+    # photons are not scattered
+    r = oracle.step_one(msc_world, W.GAMMA, oracle.make_track(z=0.0, e=e, nia=1e6, slab=0))
+    assert r["lim"] == oracle.LIM_Z and (r["track"]["dx"], r["track"]["dy"]) == (0.0, 0.0)
+
+
+def test_msc_v1_unchanged(oworld, otables):
+    # the v1 world takes the same steps as before: no scattering limit, no deflection
+    w1 = oracle.World(W.single_slab(5000.0, material=0), otables, seed=1, msc=False)
+    r = oracle.step_one(w1, W.E_MINUS, oracle.make_track(z=0.0, e=50.0, nia=1e6, slab=0))
+    assert r["lim"] == oracle.LIM_LOSS
+    assert (r["track"]["dx"], r["track"]["dy"], r["track"]["dz"]) == (0.0, 0.0, 1.0)
+
+
+@pytest.mark.parametrize("e,mat", [(20.0, 0), (100.0, 0), (1000.0, 0), (100.0, 1)])
+def test_msc_deflection_highland(otables, e, mat):
+    # after one scattering-limited step along +z, 1 - cos(theta) over theta0^2 (Highland
+    # at the step's own length, FP64) is exponential with mean 1 (the small-angle Gaussian
+    # law: theta^2 / 2 has mean theta0^2), the azimuth is uniform, and both come from
+    # Philox block 66 of the step (first uniform -> theta, second -> phi)
+    msc_world = oracle.World(W.single_slab(5000.0, material=mat), otables, seed=1, msc=True)
+    x0, dedx = (X0_PB, 1.274) if mat == 0 else (X0_LAR, 0.2105)
+    n = 20000
+    w = np.empty(n)
+    phi = np.empty(n)
+    s = None
+    for i in range(n):
+        r = oracle.step_one(msc_world, W.E_MINUS,
+                            oracle.make_track(z=0.0, e=e, nia=1e6, slab=0, id=i))
+        t = r["track"]
+        assert r["lim"] == oracle.LIM_MSC and r["alive"]
+        s = float(t["len"]) if s is None else s
+        d = np.array([t["dx"], t["dy"], t["dz"]], dtype=np.float64)
+        assert np.linalg.norm(d) == pytest.approx(1.0, abs=2e-6)
+        w[i] = 1.0 - d[2]
+        phi[i] = np.arctan2(d[1], d[0]) % (2 * np.pi)
+        if i < 500:
+            u = _block_uniforms(i, 0, 66)
+            th0 = highland_theta0(e, s, x0)
+            assert w[i] == pytest.approx(th0 * th0 * -np.log(u[0]), rel=2e-3, abs=1e-6), i
+            dphi = abs(phi[i] - 2 * np.pi * u[1])
+            assert min(dphi, 2 * np.pi - dphi) < 1e-3, i
+    th0 = highland_theta0(e, s, x0)
+    assert stats.kstest(w / th0**2, "expon").pvalue > 1e-3
+    assert np.mean(w) / th0**2 == pytest.approx(1.0, abs=4.0 / np.sqrt(n))
+    assert stats.kstest(phi, "uniform", args=(0.0, 2 * np.pi)).pvalue > 1e-3
+    # the step length the width was computed for
+    assert s == pytest.approx(MSC_FR * e / dedx, rel=1e-6)
+
+
+def test_msc_width_scales_with_thickness(otables):
+    # a 1 GeV electron crossing a lead slab of exactly one radiation length into the next
+    # (the geometry limit wins: F_R E / dEdx = 31 mm): ln x = 0, so theta0 is
+    # 13.6 MeV / (beta c p) exactly
+    slab = {"thickness": np.array([X0_PB, 100.0]), "material": np.array([0, 0], np.uint8),
+            "half_xy": 1.0e6}
+    wld = oracle.World(slab, otables, seed=1, msc=True)
+    n = 20000
+    w = np.empty(n)
+    for i in range(n):
+        r = oracle.step_one(wld, W.E_MINUS,
+                            oracle.make_track(z=0.0, e=1000.0, nia=1e6, slab=0, id=i))
+        assert r["lim"] == oracle.LIM_Z
+        w[i] = 1.0 - float(r["track"]["dz"])
+    pbc = 1000.0 * (1000.0 + 2 * MC2) / (1000.0 + MC2)
+    th0 = 13.6 / pbc
+    assert stats.kstest(w / th0**2, "expon").pvalue > 1e-3
+
+
+def test_msc_run_invariants(geom, otables):
+    p = W.small_electrons()
+    r1 = oracle.run(geom, p, seed=1, tables=otables)
+    r2 = oracle.run(geom, p, seed=1, tables=otables, msc=True, idlog=True)
+    assert _ledger_rel(r2) < 1e-12
+    c = r2["counts"].astype(np.int64)
+    assert np.array_equal(c.sum(0), r2["steps"].astype(np.int64))
+    assert len(r2["idlog"]) == int(r2["tracks"].sum())
+    # more charged steps, the same photon physics; the showers stay contained
+    assert r2["steps"][0] > 3 * r1["steps"][0] and r2["steps"][1] > 3 * r1["steps"][1]
+    assert r2["score"].sum() > 0.95 * 16 * 1000.0
+
+
+def test_msc_fp64_reference_agrees_with_strict(geom, otables):
+    p = W.mixed_primaries(400)
+    p["ekin"] = np.minimum(p["ekin"], np.float32(2000.0))
+    n = 400
+    r32 = oracle.run(geom, p, n_events=n, seed=1, tables=otables, msc=True, nthreads=8)
+    r64 = oracle.run(geom, p, n_events=n, seed=1, tables=otables, msc=True, nthreads=8,
+                     mode=oracle.REF_FP64)
+    a = r32["score"].reshape(n, -1, 2).sum(2)
+    b = r64["score"].reshape(n, -1, 2).sum(2)
+    se = np.sqrt(a.var(0, ddof=1) / n + b.var(0, ddof=1) / n)
+    d = np.abs(a.mean(0) - b.mean(0))
+    assert np.all(d <= 3 * se + 1e-9)
+    big = b.mean(0) >= 0.01 * b.mean(0).sum()
+    assert np.all(d[big] / b.mean(0)[big] <= 0.01)
+
+
 def test_geometry_limits(oworld):
     # photon along +z from the front face: stops exactly on the first plane, enters slab 1
     tr = oracle.make_track(z=0.0, d=(0.0, 0.0, 1.0), e=1.0, nia=1e6, slab=0)
