@@ -5,10 +5,10 @@
 //
 //  dense double buffer: per type, track i of the current array is stepped and
 //    its survivor and secondaries are appended to the next array.  Slots are
-//    handed out by warp-aggregated allocation: one inclusive warp scan over
-//    per-lane counts packed 10 bits per type, then one 64-bit atomicAdd for the
-//    e- and gamma counters and one for e+ per warp, so a warp's records land
-//    contiguously.
+//    handed out by warp-aggregated allocation: ballots of the per-lane counts
+//    (their population counts give the warp's total and each lane's prefix),
+//    then one 64-bit atomicAdd for the e- and gamma counters and one for e+ per
+//    warp, so a warp's records land contiguously.
 //  sparse single buffer: per type, one slot array plus two slot lists (current,
 //    next).  A survivor is updated in place (only the leaves the step changed)
 //    and its slot appended to the next list; secondaries get fresh slots from a
@@ -70,15 +70,33 @@ __device__ Tabs stage_tables(unsigned char* sm, const Args& a) {
   return tb;
 }
 
-// inclusive warp scan of packed per-type counts (10 bits per type)
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t u = __shfl_up_sync(FULL, v, d);
-    if (lane >= (uint32_t)d) v += u;
-  }
-  return v;
+// %lanemask_lt: the bits of the lanes below this one
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
 }
+
+// Per-type record counts of a lane, packed 10 bits per type (e- bits 0-9, e+ 10-19,
+// gamma 20-29).  A step makes at most one e- record (a survivor, or the electron of a
+// Compton scattering, a pair or a photoabsorption), at most one e+ record (a survivor, or
+// the positron of a pair), and at most three photons (a survivor; the two photons of a
+// below-cut positron's annihilation, after a bremsstrahlung photon in a positron step),
+// so the counts sit in bit 0, bit 10 and bits 20-21.  One ballot per such bit gives the
+// warp's counts (population counts) and each lane's exclusive prefix (population count
+// of the lanes below), the bit-1 photon ballot weighted by two.
+struct WarpCounts {
+  uint32_t total, below;  // the warp's counts and the lane's exclusive prefix, packed alike
+  __device__ __forceinline__ WarpCounts(uint32_t packed, uint32_t lt) {
+    const uint32_t be = __ballot_sync(0xffffffffu, packed & 1u);
+    const uint32_t bp = __ballot_sync(0xffffffffu, packed & (1u << 10));
+    const uint32_t bg0 = __ballot_sync(0xffffffffu, packed & (1u << 20));
+    const uint32_t bg1 = __ballot_sync(0xffffffffu, packed & (2u << 20));
+    total = __popc(be) | (__popc(bp) << 10) | ((__popc(bg0) + 2u * __popc(bg1)) << 20);
+    below = __popc(be & lt) | (__popc(bp & lt) << 10) |
+            ((__popc(bg0 & lt) + 2u * __popc(bg1 & lt)) << 20);
+  }
+};
 
 // Reserve per-type runs for a warp: returns the lane's first index per type.  `row` is a
 // count row in cw() word order: e- and gamma are reserved together by one 64-bit
@@ -86,12 +104,10 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
 // 32-bit one; a warp thus makes one atomic request in the common case.
 __device__ __forceinline__ void warp_reserve(uint32_t packed, uint32_t lane, uint32_t* row,
                                              uint32_t& p0, uint32_t& p1, uint32_t& p2) {
-  const uint32_t incl = warp_incl_scan(packed, lane);
-  const uint32_t total = __shfl_sync(FULL, incl, 31);
-  const uint32_t excl = incl - packed;
+  const WarpCounts wc(packed, lanemask_lt());
   uint32_t b0 = 0, b1 = 0, b2 = 0;
   if (lane == 0) {
-    const uint32_t ne = total & 1023u, np = (total >> 10) & 1023u, ng = (total >> 20) & 1023u;
+    const uint32_t ne = wc.total & 1023u, np = (wc.total >> 10) & 1023u, ng = wc.total >> 20;
     if (ne | ng) {
       const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(row),
                                                (unsigned long long)ne | ((unsigned long long)ng << 32));
@@ -100,9 +116,9 @@ __device__ __forceinline__ void warp_reserve(uint32_t packed, uint32_t lane, uin
     }
     if (np) b1 = atomicAdd(row + cw(EP), np);
   }
-  p0 = __shfl_sync(FULL, b0, 0) + (excl & 1023u);
-  p1 = __shfl_sync(FULL, b1, 0) + ((excl >> 10) & 1023u);
-  p2 = __shfl_sync(FULL, b2, 0) + ((excl >> 20) & 1023u);
+  p0 = __shfl_sync(FULL, b0, 0) + (wc.below & 1023u);
+  p1 = __shfl_sync(FULL, b1, 0) + ((wc.below >> 10) & 1023u);
+  p2 = __shfl_sync(FULL, b2, 0) + (wc.below >> 20);
 }
 
 // Next position of the run of type ty, advanced by one.  Written with selects and
@@ -130,14 +146,12 @@ __device__ __forceinline__ T sel3(int ty, T v0, T v1, T v2);
 __device__ __forceinline__ void sparse_reserve(const Args& a, uint32_t packed, uint32_t lane,
                                                SlotRuns& sr) {
   DevCtl* c = a.ctl;
-  const uint32_t incl = warp_incl_scan(packed, lane);
-  const uint32_t total = __shfl_sync(FULL, incl, 31);
-  const uint32_t excl = incl - packed;
+  const WarpCounts wc(packed, lanemask_lt());
   const bool reuse = a.free_ring[0] != nullptr;
 #pragma unroll
   for (int t = 0; t < 3; ++t) {
     uint32_t rb = 0, got = 0, fresh = 0;
-    const uint32_t k = (total >> (10 * t)) & 1023u;
+    const uint32_t k = (wc.total >> (10 * t)) & 1023u;
     if (lane == 0 && k) {
       if (reuse) {
         rb = atomicAdd(&c->free_head[cw(t)], k);
@@ -150,9 +164,9 @@ __device__ __forceinline__ void sparse_reserve(const Args& a, uint32_t packed, u
     sr.got[t] = __shfl_sync(FULL, got, 0);
     sr.fresh[t] = __shfl_sync(FULL, fresh, 0);
   }
-  sr.pos0 = excl & 1023u;
-  sr.pos1 = (excl >> 10) & 1023u;
-  sr.pos2 = (excl >> 20) & 1023u;
+  sr.pos0 = wc.below & 1023u;
+  sr.pos1 = (wc.below >> 10) & 1023u;
+  sr.pos2 = wc.below >> 20;
 }
 
 // The lane's next slot of type ty.
@@ -492,7 +506,6 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     inter = transport<MODE>(type, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
   }
   if (batch) {
-    finish<L, INSTR, DENSE>(a, type, it, lane, valid && !inter, t, o, slot, tl);
     const uint32_t mask = __ballot_sync(FULL, inter);
     if (inter) {
       const uint32_t pos = (wq.head + wq.count + __popc(mask & ((1u << lane) - 1u))) % QCAP;
@@ -501,13 +514,15 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     wq.count += (uint32_t)__popc(mask);
     __syncwarp();
   }
-  bool once = !batch;
+  // pass 0 finishes this chunk's own lanes (batch: those without an interaction, the
+  // others are queued; otherwise all, interactions in place); later passes drain the queue
+  bool once = true;
   while (once || wq.count >= 32u || (drain_all && wq.count)) {
     bool act, do_int;
     uint32_t n = 0, s2 = slot;
     if (once) {
-      act = valid;  // this chunk's own lanes, interactions in place
-      do_int = inter;
+      act = batch ? valid && !inter : valid;
+      do_int = !batch && inter;
     } else {
       n = wq.count >= 32u ? 32u : wq.count;  // the n oldest queued entries, one per lane
       act = lane < n;
@@ -539,7 +554,7 @@ __device__ __forceinline__ WarpQueue warp_queue(unsigned char* smem, int n_mat) 
 // photon kernels spill a few bytes), 5-7 % faster than two on large iterations.  The
 // sparse form keeps its free register budget: capped at 80 it runs 20 % slower.
 template <int TYPE, int MODE, int L, bool INSTR, bool DENSE>
-__global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_step(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(256, DENSE ? (TYPE == EM ? 4 : 3) : 1) k_step(const __grid_constant__ Args a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Tabs tb = stage_tables<TYPE == GAM, TYPE != GAM>(smem, a);
   const DevCtl* ctl = a.ctl;
@@ -635,28 +650,29 @@ __global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_transport(const __grid_c
       inter = transport<MODE>(TYPE, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
     }
     finish<L, false, DENSE>(a, TYPE, it, lane, valid && !inter, t, o, slot, tl);
-    // queue positions: one inclusive scan of per-queue counts packed 10 bits per queue,
-    // then one atomicAdd per non-empty queue
+    // queue positions: one ballot per queue (a lane enters at most one), then one
+    // atomicAdd per non-empty queue
     const int k = (TYPE == GAM && inter) ? photon_queue(cx) - IQ_COMPTON : 0;
-    const uint32_t packed = inter ? 1u << (10 * k) : 0u;
-    const uint32_t incl = warp_incl_scan(packed, lane);
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    uint32_t b[3] = {0u, 0u, 0u};
+    const uint32_t lt = lanemask_lt();
+    uint32_t b[3] = {0u, 0u, 0u}, mk[3] = {0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < Q::count; ++j) mk[j] = __ballot_sync(FULL, inter && k == j);
     if (lane == 0) {
 #pragma unroll
-      for (int j = 0; j < Q::count; ++j) {
-        const uint32_t m = (total >> (10 * j)) & 1023u;
-        if (m) b[j] = atomicAdd(&ctl->iq_n[Q::first + j], m);
-      }
+      for (int j = 0; j < Q::count; ++j)
+        if (mk[j]) b[j] = atomicAdd(&ctl->iq_n[Q::first + j], (uint32_t)__popc(mk[j]));
     }
-    uint32_t base = 0;
+    uint32_t base = 0, below = 0;
 #pragma unroll
     for (int j = 0; j < Q::count; ++j) {
       const uint32_t bj = __shfl_sync(FULL, b[j], 0);
-      if (j == k) base = bj;
+      if (j == k) {
+        base = bj;
+        below = __popc(mk[j] & lt);
+      }
     }
     if (inter) {
-      const uint32_t at = base + (((incl - packed) >> (10 * k)) & 1023u);
+      const uint32_t at = base + below;
       if (at < a.cap) q_put(queue_of<TYPE>(a, k), (size_t)a.cap, at, t, cx, slot);
       else atomicOr(&ctl->status, ST_CAPACITY);
     }
