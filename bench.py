@@ -62,6 +62,8 @@ def parse_args(argv=None):
                     help="default: the autotuner's pick for the workload, else persistent for"
                          " the single showers and hybrid for the mixed primaries")
     ap.add_argument("--mode", default="strict", choices=["strict", "fast"])
+    ap.add_argument("--msc", action="store_true",
+                    help="the toy model v2: multiple scattering of e+- (default: v1)")
     ap.add_argument("--block-size", type=int, default=None)
     ap.add_argument("--capacity-log2", type=int, default=None,
                     help="track slots per type: 2^N (default per workload: 16, 22, 24, 26)")
@@ -72,7 +74,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-rate", type=float, default=200.0)
-    ap.add_argument("--serving-events", type=int, default=200)
+    ap.add_argument("--serving-events", type=int, default=1000)
     a = ap.parse_args(argv)
     if a.config is not None:
         a.workload = {1: "small", 2: "jittered", 3: "mixed", 4: "uneven"}[a.config]
@@ -131,7 +133,7 @@ def aggregate(local_steps: float, local_seconds: float, group):
 
 # ------------------------------------------------------------------ inputs
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, msc: bool = False):
     from paper_2302_08252_gb300 import workloads as W
     if name == "jittered":
         p = W.jittered_electrons(seed=W.PRIMARY_SEED + rank)
@@ -147,6 +149,8 @@ def make_workload(name: str, rank: int):
         desc = ("256 events of 1-1000 mixed e-/e+/gamma primaries (0.1-100 GeV), "
                 "50x(2.3 mm Pb + 5.7 mm lAr)")
     n_events = int(p["event"].max()) + 1
+    if msc:
+        desc += "; toy model v2 (multiple scattering of e+-)"
     return W.calorimeter(), p, n_events, desc
 
 
@@ -254,7 +258,8 @@ def run_config(et, geom, prim, n_events, args, form, layout, driver, steps, warm
                           form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
                           layout=layout, driver=driver,
                           mode=et.MODE_STRICT if args.mode == "strict" else et.MODE_FAST,
-                          block_size=args.block_size, seed=1, reuse_slots=reuse_slots)
+                          block_size=args.block_size, seed=1, reuse_slots=reuse_slots,
+                          msc=args.msc)
     d_prim = torch.from_numpy(prim.view(np.uint8).copy()).cuda()
     n = len(prim)
     stream = torch.cuda.current_stream()
@@ -312,10 +317,11 @@ def e2e_measure(et, ctx, prim, n_events, n_slabs, steps):
 
 def serving_measure(geom, args):
     """Continuous batching under a Poisson stream of uneven events (1-1000 primaries of
-    mixed types, 0.1-100 GeV each): p50/p99 arrival-to-result latency and sustained
-    track-steps/s, tuned form (persistent driver, whatever --driver says: the serving
-    loop runs a few iterations per round, where one launch per round pays most) and the
-    plain sparse single buffer on the same stream."""
+    mixed types, 0.1-100 GeV each) through the library's native serving loop: p50/p99
+    arrival-to-result latency over the events after the first 10 % (warm-up) and
+    sustained track-steps/s, tuned form (persistent driver, whatever --driver says: a
+    round runs a few iterations, where one launch per round pays most) and the plain
+    sparse single buffer on the same stream."""
     from paper_2302_08252_gb300 import serving
     reqs = serving.poisson_requests(args.serving_rate, args.serving_events)
     out = {"rate_per_s": args.serving_rate, "events": args.serving_events,
@@ -329,7 +335,8 @@ def serving_measure(geom, args):
         out[name] = {"form": form, "layout": layout, "driver": driver,
                      "p50_ms": 1e3 * q["p50"], "p99_ms": 1e3 * q["p99"],
                      "steps_per_s": st.steps / st.wall, "wall_s": st.wall,
-                     "max_inflight": st.max_inflight, "rounds": st.rounds}
+                     "max_inflight": st.max_inflight, "rounds": st.rounds,
+                     "latency_events": len(st.results) - int(0.1 * len(st.results))}
         del srv
     return out
 
@@ -349,19 +356,19 @@ def oracle_sample(workload: str, prim, n_events: int, reference: bool):
     return prim, "whole workload"
 
 
-def cpu_baseline(geom, prim, n_events, workload, one_thread_primaries=50):
+def cpu_baseline(geom, prim, n_events, workload, one_thread_primaries=50, msc=False):
     """The oracle on the host cores (a bounded sample of the workload on every core), and
     under "one_thread" its first one_thread_primaries primaries on one thread."""
     import oracle
     sample, what = oracle_sample(workload, prim, n_events, reference=False)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
+    r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores, msc=msc)
     dt = time.perf_counter() - t0
     steps = int(r["steps"].sum())
     sample1 = sample[:one_thread_primaries].copy()
     t1 = time.perf_counter()
-    r1 = oracle.run(geom, sample1, n_events=n_events, seed=1, nthreads=1)
+    r1 = oracle.run(geom, sample1, n_events=n_events, seed=1, nthreads=1, msc=msc)
     dt1 = time.perf_counter() - t1
     steps1 = int(r1["steps"].sum())
     return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -378,16 +385,16 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    geom, prim, n_events, desc = make_workload(args.workload, 0)
+    geom, prim, n_events, desc = make_workload(args.workload, 0, args.msc)
     # a bounded sample: about a second of host-core work per step
     sample, what = oracle_sample(args.workload, prim, n_events, reference=True)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
+        oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores, msc=args.msc)
     secs, steps = 0.0, 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores)
+        r = oracle.run(geom, sample, n_events=n_events, seed=1, nthreads=cores, msc=args.msc)
         secs += time.perf_counter() - t0
         steps += int(r["steps"].sum())
     value = steps / secs
@@ -413,7 +420,7 @@ def ours_arm(args, rank, world, group):
 
     from paper_2302_08252_gb300 import et
     dev = torch.cuda.current_device()
-    geom, prim, n_events, desc = make_workload(args.workload, rank)
+    geom, prim, n_events, desc = make_workload(args.workload, rank, args.msc)
     n_slabs = len(geom["thickness"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     uuid = None
@@ -448,7 +455,7 @@ def ours_arm(args, rank, world, group):
         runs_per_launch = args.steps / tuned["kernel_launches"]
         alg_per_launch = algorithmic_bytes(steps_per_run, tuned["n_prim"]) * runs_per_launch
         achieved = alg_per_launch / (per_launch_ms / 1e3) / 1e9
-    key = f"{args.mode}/{args.form}/{args.layout}/{args.driver}"
+    key = f"{args.mode}/{args.form}/{args.layout}/{args.driver}" + ("/msc" if args.msc else "")
     tr = committed_traffic(key)
     traffic = tr * steps_per_run * (args.steps / max(1, tuned["kernel_launches"])) if tr else None
 
@@ -459,6 +466,7 @@ def ours_arm(args, rank, world, group):
         "data": "synthetic",
         "config": {"workload": desc, "form": args.form, "layout": args.layout,
                    "driver": args.driver, "mode": args.mode, "block_size": args.block_size,
+                   "physics": "toy model v2 (multiple scattering)" if args.msc else "toy model v1",
                    "steps_per_run": steps_per_run,
                    "iterations_per_run": tuned["iterations"] // args.steps,
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
@@ -492,10 +500,10 @@ def ours_arm(args, rank, world, group):
                              "driver": "hostloop", "steps": args.plain_steps,
                              "reuse_slots": reuse}
             line["tuned_vs_plain"] = value / pv
-        if not args.no_serving:
+        if not args.no_serving and not args.msc:
             line["serving"] = serving_measure(geom, args)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events, args.workload)
+            line["cpu_baseline"] = cpu_baseline(geom, prim, n_events, args.workload, msc=args.msc)
     line["clocks"] = summarize_clocks(clock_rows, t_wall0, t_wall1)
     if rank == 0:
         print(json.dumps(line), flush=True)

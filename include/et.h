@@ -105,6 +105,12 @@ typedef struct {
                                warps.  Same histories as the fused step.  Needs 96 bytes x
                                2^capacity_log2 per process queue (5 queues); not with
                                ET_DRIVER_PERSISTENT or instrument (ET_ERR_INVALID). */
+  int32_t msc;              /* 0: the toy model (v1); 1: the toy model v2, which adds multiple
+                               scattering of e+-: a step limit of 0.04 max(T/dEdx, 0.5 mm)
+                               and a deflection of Highland's width after every step (the
+                               multiple-scattering fields of the paper's Sec. 5 electron
+                               trace).  Needs the radiation lengths (et_load_msc) before the
+                               first injection. */
 } et_config;
 
 /* Create a context (allocates the track buffers).  *out is NULL on failure. */
@@ -132,6 +138,18 @@ et_status et_create_geometry(et_ctx* ctx, uint32_t n_slabs, const double* thickn
  */
 et_status et_load_tables(et_ctx* ctx, uint32_t n_materials, uint32_t n_nodes, float log_emin,
                          float inv_dlog, const float* sigma, const float* dedx);
+
+/*
+ * Radiation lengths X0 (mm) per material, for the multiple scattering of the toy model
+ * v2 (et_config.msc = 1): the width 13.6 MeV / (beta c p) sqrt(s/X0) (1 + 0.038 ln(s/X0))
+ * of Highland's formula.  Call after et_load_tables (same n_materials), before the
+ * first injection; ET_ERR_STATE on a v1 context or out of order, ET_ERR_INVALID for
+ * values that are not positive and finite.
+ */
+et_status et_load_msc(et_ctx* ctx, uint32_t n_materials, const float* x0_mm);
+
+/* The toy model's radiation lengths (FP32 of 5.612 mm lead, 140 mm liquid argon). */
+et_status et_toy_radiation_lengths(uint32_t n_materials, float* x0_out);
 
 /*
  * The toy model's own tables, computed on the host from the FP64 closed forms
@@ -291,6 +309,41 @@ et_status et_poll_completed(et_ctx* ctx, uint32_t* events, uint64_t cap, uint64_
 /* Serving: clear an event's scores, ledger and live count so that its number can be
  * given to a new event (call after reading its results). */
 et_status et_release_event(et_ctx* ctx, uint32_t event);
+
+/*
+ * Native serving loop (continuous batching, the paper's AdePT offload pattern of Sec. 1
+ * and 2: a host hands over events while others are in flight; each iteration advances
+ * every active track of every event).  Serving contexts only (cfg.serving = 1).
+ *
+ * et_serve_submit queues one event's n primaries (host memory, copied; every primary's
+ * .event == event < max_events) with its reserve: the track slots per type
+ * (e-, e+, gamma) the event may occupy at its peak.  Requests are admitted in submission
+ * order while the reserves of the events in flight fit into 90 % of the capacity per
+ * type (the first one is always admitted), and never while an event of the same number
+ * is in flight.  ET_ERR_CAPACITY: a reserve above the capacity.
+ *
+ * et_serve_round runs one round: it admits and injects what fits, runs `iters`
+ * iterations with every shower in flight (the persistent driver launches them
+ * asynchronously; the other drivers read counts back between iterations), and queues a
+ * collection of the events completed so far (their per-slab deposits and ledgers are
+ * copied out and cleared on the device, so their numbers can be given to new events).
+ * It then waits for the previous round and returns that round's completions:
+ * events[n_out], rows[n_out][n_slabs + 5] = per-slab deposits, then the ledger injected,
+ * below-cut, escaped, mass created, mass consumed (MeV); steps (optional) the track-steps
+ * the previous round took; in_flight (optional) the events admitted or queued and not yet
+ * returned.  Round k's GPU work is queued before round k - 1 is waited for, so the host's
+ * admission and read-back overlap the GPU.  cap >= et_serve_capacity's max_results.
+ * et_serve_flush waits for the last round and returns its completions (call when no
+ * more requests come, until in_flight is 0, with rounds in between).
+ */
+et_status et_serve_submit(et_ctx* ctx, const et_primary* primaries, size_t n, uint32_t event,
+                          const uint32_t reserve[3]);
+et_status et_serve_round(et_ctx* ctx, uint32_t iters, uint32_t* events, double* rows,
+                         uint64_t cap, uint64_t* n_out, uint64_t* steps, uint32_t* in_flight);
+et_status et_serve_flush(et_ctx* ctx, uint32_t* events, double* rows, uint64_t cap,
+                         uint64_t* n_out, uint64_t* steps, uint32_t* in_flight);
+/* The most completions one round returns (the result buffers' row count). */
+et_status et_serve_capacity(et_ctx* ctx, uint32_t* max_results);
 
 /*
  * Timing of the step kernels (CUDA events on the context's stream around every

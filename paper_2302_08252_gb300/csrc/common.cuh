@@ -16,7 +16,7 @@
 namespace et {
 
 enum { EM = 0, EP = 1, GAM = 2, NTYPES = 3 };
-enum { LIM_Z = 0, LIM_X = 1, LIM_Y = 2, LIM_LOSS = 3, LIM_PHYS = 4 };
+enum { LIM_Z = 0, LIM_X = 1, LIM_Y = 2, LIM_LOSS = 3, LIM_PHYS = 4, LIM_MSC = 5 };
 enum { PROC_NONE = 0, PROC_COMPTON = 1, PROC_PAIR = 2, PROC_PHOT = 3, PROC_BREM = 4 };
 enum { ALIVE = 0, DEATH_ESCAPE = 1, DEATH_CUT = 2, DEATH_ABSORB = 3 };
 enum { MODE_STRICT = 0, MODE_FAST = 1 };
@@ -150,6 +150,8 @@ struct Args {
   const uint8_t* mat;           // [n_slabs]
   float half_xy, log_emin, inv_dlog;
   float dedx[4];
+  int32_t msc;                  // toy model v2: multiple scattering of e+- (0: v1)
+  float x0[4];                  // radiation lengths (mm), v2 only
   uint32_t seed_lo;
   IdRec* idlog;                 // NULL: off
   unsigned long long idlog_cap;

@@ -10,11 +10,14 @@
 // mirrors the plain AdePT loop (launch per type, read counts back).
 #define ET_HOST_TU
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "et.h"
@@ -32,6 +35,44 @@ struct EventPair {
   cudaEvent_t a, b;
 };
 
+// The native serving loop's state (et_serve_*), created on first use.
+struct ServeReq {
+  std::vector<Primary> p;
+  uint32_t event;
+  uint32_t reserve[3];
+};
+
+struct ServeState {
+  std::deque<ServeReq> pending;
+  std::unordered_map<uint32_t, std::array<uint32_t, 3>> inflight;  // event -> reserve
+  uint64_t reserved[3] = {0, 0, 0};
+  uint32_t max_out = 0;
+  uint32_t* d_cursor = nullptr;  // collection cursor in the completion ring
+  uint32_t* d_events = nullptr;  // [max_out + 1]
+  double* d_rows = nullptr;      // [max_out][n_slabs + 5]
+  uint32_t* h_events[2] = {nullptr, nullptr};  // pinned, one per round parity
+  double* h_rows[2] = {nullptr, nullptr};
+  DevCtl* h_ctl[2] = {nullptr, nullptr};
+  uint32_t* h_rel[2] = {nullptr, nullptr};     // pinned iteration limits of the rounds
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  uint64_t issued = 0, delivered = 0;          // rounds
+  uint64_t steps_seen = 0;                     // cumulative steps at the last delivery
+  std::vector<Primary> batch;
+};
+
+static void serve_free(ServeState* s) {
+  if (!s) return;
+  for (int k = 0; k < 2; ++k) {
+    if (s->h_events[k]) cudaFreeHost(s->h_events[k]);
+    if (s->h_rows[k]) cudaFreeHost(s->h_rows[k]);
+    if (s->h_ctl[k]) cudaFreeHost(s->h_ctl[k]);
+    if (s->h_rel[k]) cudaFreeHost(s->h_rel[k]);
+    if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+  }
+  delete s;
+}
+
+
 struct et_ctx {
   et_config cfg{};
   std::string err;
@@ -46,7 +87,7 @@ struct et_ctx {
   DevCtl* h_ctl = nullptr;  // pinned
   uint32_t* h_stop = nullptr;  // pinned scratch for stop_iter uploads
   double* h_ledger = nullptr;  // pinned staging of the ledgers (allocated on first read)
-  bool have_geom = false, have_tables = false;
+  bool have_geom = false, have_tables = false, have_msc = false;
   std::vector<float> planes;
   std::vector<uint8_t> mat;
   Primary* d_stage = nullptr;
@@ -62,6 +103,7 @@ struct et_ctx {
   size_t smem_all = 0, smem_tab = 0;
   size_t smem_step[3] = {0, 0, 0};  // per-type step kernels: the e+- kernels queue nothing
   bool split = false;
+  ServeState* serve = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
   bool timing = false;
@@ -206,7 +248,8 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
       k.max_events == 0 || (k.instrument && k.mode != ET_MODE_STRICT) || (k.seed >> 32) != 0 ||
       ((k.alloc == nullptr) != (k.free == nullptr)) ||
       (k.split_interactions != 0 && k.split_interactions != 1) ||
-      (k.split_interactions && (k.driver == ET_DRIVER_PERSISTENT || k.instrument)))
+      (k.split_interactions && (k.driver == ET_DRIVER_PERSISTENT || k.instrument)) ||
+      (k.msc != 0 && k.msc != 1))
     return ET_ERR_INVALID;
   et_ctx* c = new et_ctx();
   c->cfg = k;
@@ -281,6 +324,7 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
     }
   }
   a.seed_lo = (uint32_t)k.seed;
+  a.msc = k.msc;
   a.timeout_ns = 2000000000ull;
   if (cudaMallocHost(&c->h_ctl, sizeof(DevCtl)) != cudaSuccess ||
       cudaMallocHost(&c->h_stop, 64) != cudaSuccess) {
@@ -308,6 +352,7 @@ et_status et_destroy(et_ctx* c) {
   if (c->h_ledger) cudaFreeHost(c->h_ledger);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_stage_done) cudaEventDestroy(c->h_stage_done);
+  serve_free(c->serve);
   (void)cudaGetLastError();
   delete c;
   return ET_OK;
@@ -332,6 +377,15 @@ et_status et_reset(et_ctx* c) {
   // kernel timings recorded so far are collected at the next read-back
   c->launches = 0;
   memset(c->h_ctl, 0, sizeof(DevCtl));
+  if (c->serve) {  // the serving loop starts over: nothing queued, in flight or collected
+    ServeState* sv = c->serve;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    sv->pending.clear();
+    sv->inflight.clear();
+    for (int t = 0; t < 3; ++t) sv->reserved[t] = 0;
+    sv->issued = sv->delivered = sv->steps_seen = 0;
+    CUDA_TRY(c, cudaMemsetAsync(sv->d_cursor, 0, 4, c->stream));
+  }
   return ET_OK;
 }
 
@@ -453,9 +507,25 @@ et_status et_load_tables(et_ctx* c, uint32_t n_materials, uint32_t n_nodes, floa
   return ET_OK;
 }
 
+et_status et_load_msc(et_ctx* c, uint32_t n_materials, const float* x0_mm) {
+  if (!c) return ET_ERR_INVALID;
+  if (!c->cfg.msc) return fail(c, ET_ERR_STATE, "radiation lengths: not a multiple-scattering context");
+  if (!c->have_tables || c->have_msc)
+    return fail(c, ET_ERR_STATE, "radiation lengths: once, after the tables");
+  if (!x0_mm || n_materials != c->args.n_mat)
+    return fail(c, ET_ERR_INVALID, "radiation lengths: one per material");
+  for (uint32_t m = 0; m < n_materials; ++m)
+    if (!(x0_mm[m] > 0.0f) || !std::isfinite(x0_mm[m]))
+      return fail(c, ET_ERR_INVALID, "radiation length %u", m);
+  for (uint32_t m = 0; m < n_materials; ++m) c->args.x0[m] = x0_mm[m];
+  c->have_msc = true;
+  return ET_OK;
+}
+
 et_status et_inject(et_ctx* c, const et_primary* p, size_t n) {
   if (!c) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   if (n == 0) return ET_OK;
   if (!p || n > c->cap) return fail(c, ET_ERR_INVALID, "bad primaries");
   const float h = c->args.half_xy;
@@ -509,7 +579,8 @@ et_status et_inject(et_ctx* c, const et_primary* p, size_t n) {
 
 et_status et_inject_device(et_ctx* c, const et_primary* p, size_t n) {
   if (!c) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   if (n == 0) return ET_OK;
   if (!p || n > c->cap || ((uintptr_t)p & 15u) != 0) return fail(c, ET_ERR_INVALID, "bad primaries");
   for (uint32_t s = 0; s < c->args.n_slabs; ++s)
@@ -588,7 +659,8 @@ static void fill_stats(et_ctx* c, const DevCtl& before, et_iter_stats* out) {
 
 et_status et_run_iteration(et_ctx* c, et_iter_stats* out) {
   if (!c) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   const DevCtl before = *c->h_ctl;
@@ -726,7 +798,8 @@ static et_status run_hybrid(et_ctx* c, uint64_t max_iters, et_iter_stats* totals
 et_status et_run_until_empty(et_ctx* c, uint64_t max_iters, et_iter_stats* totals,
                              uint64_t* n_iters) {
   if (!c) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   if (c->cfg.driver == ET_DRIVER_HYBRID) return run_hybrid(c, max_iters, totals, n_iters);
   if (c->cfg.driver == ET_DRIVER_PERSISTENT && max_iters > 0) {
     // one launch, one read-back: the kernel stops after max_iters iterations (or when no
@@ -1016,7 +1089,7 @@ namespace {
 struct SnapHeader {
   char magic[8];
   uint32_t version, form, layout, capacity_log2, mode, max_events, max_iters, n_slabs;
-  uint32_t serving, reuse_slots, id_log, instrument;
+  uint32_t serving, reuse_slots, id_log, instrument, msc, pad;
   uint64_t id_log_capacity, seed, n_sections;
 };
 struct SnapSection {
@@ -1081,7 +1154,7 @@ static SnapHeader snapshot_header(const et_ctx* c, uint64_t n_sections) {
   SnapHeader hd;
   memset(&hd, 0, sizeof hd);
   memcpy(hd.magic, kSnapMagic, 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.form = (uint32_t)c->cfg.form;
   hd.layout = (uint32_t)c->cfg.layout;
   hd.capacity_log2 = c->cfg.capacity_log2;
@@ -1093,6 +1166,8 @@ static SnapHeader snapshot_header(const et_ctx* c, uint64_t n_sections) {
   hd.reuse_slots = (uint32_t)c->cfg.reuse_slots;
   hd.id_log = (uint32_t)c->cfg.id_log;
   hd.instrument = (uint32_t)c->cfg.instrument;
+  hd.msc = (uint32_t)c->cfg.msc;
+  hd.pad = 0;
   hd.id_log_capacity = c->cfg.id_log_capacity;
   hd.seed = c->cfg.seed;
   hd.n_sections = n_sections;
@@ -1101,7 +1176,8 @@ static SnapHeader snapshot_header(const et_ctx* c, uint64_t n_sections) {
 
 et_status et_snapshot_size(et_ctx* c, uint64_t* bytes) {
   if (!c || !bytes) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   uint64_t n = sizeof(SnapHeader);
@@ -1112,7 +1188,8 @@ et_status et_snapshot_size(et_ctx* c, uint64_t* bytes) {
 
 et_status et_snapshot(et_ctx* c, void* out, uint64_t cap, uint64_t* written) {
   if (!c || !out) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   const std::vector<SnapItem> items = snapshot_items(c);
@@ -1137,12 +1214,13 @@ et_status et_snapshot(et_ctx* c, void* out, uint64_t cap, uint64_t* written) {
 
 et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
   if (!c || !in) return ET_ERR_INVALID;
-  if (!c->have_geom || !c->have_tables) return fail(c, ET_ERR_STATE, "geometry and tables first");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   if (n < sizeof(SnapHeader)) return fail(c, ET_ERR_INVALID, "snapshot too short");
   SnapHeader hd;
   memcpy(&hd, in, sizeof hd);
   const SnapHeader mine = snapshot_header(c, hd.n_sections);
-  if (memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 1)
+  if (memcmp(hd.magic, kSnapMagic, 8) != 0 || hd.version != 2)
     return fail(c, ET_ERR_INVALID, "not a snapshot of this library");
   if (memcmp(&hd, &mine, sizeof hd) != 0)
     return fail(c, ET_ERR_INVALID, "snapshot of a context with another configuration");
@@ -1190,6 +1268,201 @@ et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
   s = sync_ctl(c);
   if (s != ET_OK) return s;
   c->done_read = c->h_ctl->n_done;  // completions before the snapshot were already reported
+  return ET_OK;
+}
+
+
+// ---- native serving loop: pipelined rounds of continuous batching ----
+// Requests wait in a host queue (et_serve_submit).  Each round (et_serve_round) admits
+// queued requests in order while their reserved track slots fit, injects them, runs a
+// few iterations with every in-flight shower, and lets a one-block kernel copy the
+// results of the events completed so far into a compact buffer (clearing their scores)
+// that one copy brings to pinned host memory.  The call then waits for the round before
+// it and hands back that round's results: the host's admission and read-back overlap the
+// GPU's work on the next round, which is already queued on the stream.
+static et_status serve_state(et_ctx* c, ServeState** out) {
+  if (!c->args.live) return fail(c, ET_ERR_STATE, "not a serving context");
+  if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
+    return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
+  if (!c->serve) {
+    ServeState* s = new ServeState();
+    s->max_out = c->cfg.max_events < 256u ? c->cfg.max_events : 256u;
+    const size_t row = (size_t)c->args.n_slabs + 5u;
+    s->d_cursor = (uint32_t*)dalloc(c, 256);
+    s->d_events = (uint32_t*)dalloc(c, ((size_t)s->max_out + 1u) * 4u);
+    s->d_rows = (double*)dalloc(c, (size_t)s->max_out * row * 8u);
+    bool ok = s->d_cursor && s->d_events && s->d_rows;
+    for (int k = 0; k < 2 && ok; ++k) {
+      ok = cudaMallocHost(&s->h_events[k], ((size_t)s->max_out + 1u) * 4u) == cudaSuccess &&
+           cudaMallocHost(&s->h_rows[k], (size_t)s->max_out * row * 8u) == cudaSuccess &&
+           cudaMallocHost(&s->h_ctl[k], sizeof(DevCtl)) == cudaSuccess &&
+           cudaMallocHost(&s->h_rel[k], 64) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s->ev[k], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      (void)cudaGetLastError();
+      serve_free(s);
+      return fail(c, ET_ERR_NOMEM, "serving buffers");
+    }
+    // the cursor starts at the completions already reported through et_poll_completed
+    s->h_rel[0][0] = c->done_read;
+    CUDA_TRY(c, cudaMemcpyAsync(s->d_cursor, s->h_rel[0], 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->serve = s;
+  }
+  *out = c->serve;
+  return ET_OK;
+}
+
+et_status et_serve_submit(et_ctx* c, const et_primary* p, size_t n, uint32_t event,
+                          const uint32_t reserve[3]) {
+  if (!c) return ET_ERR_INVALID;
+  ServeState* s = nullptr;
+  et_status st = serve_state(c, &s);
+  if (st != ET_OK) return st;
+  if (!p || n == 0 || !reserve || event >= c->cfg.max_events)
+    return fail(c, ET_ERR_INVALID, "et_serve_submit: bad request");
+  for (int t = 0; t < 3; ++t)
+    if (reserve[t] > c->cap) return fail(c, ET_ERR_CAPACITY, "et_serve_submit: reserve above capacity");
+  ServeReq r;
+  r.p.resize(n);
+  memcpy(r.p.data(), p, n * sizeof(Primary));
+  for (size_t i = 0; i < n; ++i)
+    if (r.p[i].event != event) return fail(c, ET_ERR_INVALID, "et_serve_submit: primary of another event");
+  r.event = event;
+  for (int t = 0; t < 3; ++t) r.reserve[t] = reserve[t];
+  s->pending.push_back(std::move(r));
+  return ET_OK;
+}
+
+// Hand back the results of round `k` (complete: its event has been waited for).
+static et_status serve_deliver(et_ctx* c, ServeState* s, uint64_t k, uint32_t* events,
+                               double* rows, uint64_t cap, uint64_t* n_out, uint64_t* steps) {
+  CUDA_TRY(c, cudaEventSynchronize(s->ev[k % 2]));
+  timing_collect(c);
+  const DevCtl& d = *s->h_ctl[k % 2];
+  const uint32_t st = d.status;
+  if (st & ST_TIMEOUT) return fail(c, ET_ERR_TIMEOUT, "device wait timed out (status 0x%x)", st);
+  if (st & ST_CAPACITY) return fail(c, ET_ERR_CAPACITY, "track buffer capacity %u exceeded", c->cap);
+  if (st & ST_BAD_PRIMARY) return fail(c, ET_ERR_INVALID, "invalid device-side primary (skipped)");
+  const uint32_t n = s->h_events[k % 2][s->max_out];
+  const size_t row = (size_t)c->args.n_slabs + 5u;
+  if (n > cap) return fail(c, ET_ERR_CAPACITY, "et_serve_round: result buffer shorter than %u", n);
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t e = s->h_events[k % 2][j];
+    events[j] = e;
+    memcpy(rows + (size_t)j * row, s->h_rows[k % 2] + (size_t)j * row, row * 8u);
+    auto it = s->inflight.find(e);
+    if (it != s->inflight.end()) {
+      for (int t = 0; t < 3; ++t) s->reserved[t] -= it->second[t];
+      s->inflight.erase(it);
+    }
+  }
+  *n_out += n;
+  const uint64_t all = d.steps[0] + d.steps[1] + d.steps[2];
+  if (steps) *steps += all - s->steps_seen;
+  s->steps_seen = all;
+  s->delivered = k + 1;
+  return ET_OK;
+}
+
+et_status et_serve_round(et_ctx* c, uint32_t iters, uint32_t* events, double* rows,
+                         uint64_t cap, uint64_t* n_out, uint64_t* steps, uint32_t* in_flight) {
+  if (!c || !n_out || (cap && (!events || !rows))) return ET_ERR_INVALID;
+  ServeState* s = nullptr;
+  et_status st = serve_state(c, &s);
+  if (st != ET_OK) return st;
+  *n_out = 0;
+  if (steps) *steps = 0;
+  if (cap < s->max_out) return fail(c, ET_ERR_INVALID, "et_serve_round: cap below %u", s->max_out);
+  // 1. admission by reserved track slots (90 % of the capacity), in submission order
+  s->batch.clear();
+  while (!s->pending.empty()) {
+    ServeReq& r = s->pending.front();
+    bool fits = true;
+    for (int t = 0; t < 3; ++t)
+      if ((double)(s->reserved[t] + r.reserve[t]) > 0.9 * (double)c->cap) fits = false;
+    if ((!fits && !s->inflight.empty()) || s->inflight.count(r.event)) break;
+    for (int t = 0; t < 3; ++t) s->reserved[t] += r.reserve[t];
+    s->inflight[r.event] = {r.reserve[0], r.reserve[1], r.reserve[2]};
+    s->batch.insert(s->batch.end(), r.p.begin(), r.p.end());
+    s->pending.pop_front();
+  }
+  const uint64_t k = s->issued;
+  if (!s->batch.empty()) {
+    st = et_inject(c, reinterpret_cast<const et_primary*>(s->batch.data()), s->batch.size());
+    if (st != ET_OK) return st;
+  }
+  // 2. the round's iterations: the persistent kernel stops after `iters` of them
+  if (iters > 0 && !s->inflight.empty()) {
+    if (c->cfg.driver == ET_DRIVER_PERSISTENT) {
+      s->h_rel[k % 2][0] = iters;
+      CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_rel, s->h_rel[k % 2], 4, cudaMemcpyHostToDevice,
+                                  c->stream));
+      int fault = c->fault_skip_block;
+      void* params[] = {(void*)&c->args, (void*)&fault};
+      const void* fn = c->ks.persistent[c->cfg.instrument ? 1 : 0][c->dense ? 1 : 0];
+      EventPair* ev = timing_begin(c);
+      CUDA_TRY(c, cudaLaunchCooperativeKernel(fn, dim3(c->grid_persistent), dim3(c->block),
+                                              params, c->smem_all, c->stream));
+      timing_end(c, ev);
+      c->launches += 1;
+    } else {
+      // the other drivers read the counts back between launches: a synchronous round
+      et_iter_stats tot;
+      uint64_t ni = 0;
+      st = et_run_until_empty(c, iters, &tot, &ni);
+      if (st != ET_OK) return st;
+    }
+  }
+  // 3. collect the completed events, copy them and the counters to pinned host memory
+  {
+    void* params[] = {(void*)&c->args, (void*)&s->d_cursor, (void*)&s->d_events,
+                      (void*)&s->d_rows, (void*)&s->max_out};
+    st = launch(c, (const void*)k_serve_collect, 1, 128, 0, params);
+    if (st != ET_OK) return st;
+  }
+  const size_t row = (size_t)c->args.n_slabs + 5u;
+  CUDA_TRY(c, cudaMemcpyAsync(s->h_events[k % 2], s->d_events, ((size_t)s->max_out + 1u) * 4u,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(s->h_rows[k % 2], s->d_rows, (size_t)s->max_out * row * 8u,
+                              cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(s->h_ctl[k % 2], c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaEventRecord(s->ev[k % 2], c->stream));
+  s->issued = k + 1;
+  // 4. the round before this one: wait for it and hand back its results
+  if (k >= 1 && s->delivered < k) {
+    st = serve_deliver(c, s, k - 1, events, rows, cap, n_out, steps);
+    if (st != ET_OK) return st;
+  }
+  if (in_flight) *in_flight = (uint32_t)(s->inflight.size() + s->pending.size());
+  return ET_OK;
+}
+
+et_status et_serve_flush(et_ctx* c, uint32_t* events, double* rows, uint64_t cap,
+                         uint64_t* n_out, uint64_t* steps, uint32_t* in_flight) {
+  if (!c || !n_out || (cap && (!events || !rows))) return ET_ERR_INVALID;
+  ServeState* s = nullptr;
+  et_status st = serve_state(c, &s);
+  if (st != ET_OK) return st;
+  *n_out = 0;
+  if (steps) *steps = 0;
+  if (cap < s->max_out) return fail(c, ET_ERR_INVALID, "et_serve_flush: cap below %u", s->max_out);
+  if (s->delivered < s->issued) {
+    st = serve_deliver(c, s, s->issued - 1, events, rows, cap, n_out, steps);
+    if (st != ET_OK) return st;
+  }
+  if (in_flight) *in_flight = (uint32_t)(s->inflight.size() + s->pending.size());
+  return ET_OK;
+}
+
+et_status et_serve_capacity(et_ctx* c, uint32_t* max_results) {
+  if (!c || !max_results) return ET_ERR_INVALID;
+  ServeState* s = nullptr;
+  et_status st = serve_state(c, &s);
+  if (st != ET_OK) return st;
+  *max_results = s->max_out;
   return ET_OK;
 }
 

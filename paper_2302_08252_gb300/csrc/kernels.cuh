@@ -32,23 +32,27 @@ namespace et {
 constexpr uint32_t FULL = 0xffffffffu;
 
 // ---- shared-memory staging of geometry and tables ----
-// layout: planes[129] | dedx[4] | mat[128] | tot[n_mat*256] (float2) | brem[..] (float2) |
-//         cp[n_mat*256] (float4)
+// layout: planes[129] | dedx[4] | x0[4] | mat[128] | tot[n_mat*256] (float2) |
+//         brem[..] (float2) | cp[n_mat*256] (float4)
 __host__ __device__ inline size_t smem_bytes(int n_mat) {
-  return 129 * 4 + 4 * 4 + 128 + (size_t)n_mat * NBINS * (8 + 8 + 16) + 16;
+  return 129 * 4 + 4 * 4 + 4 * 4 + 128 + (size_t)n_mat * NBINS * (8 + 8 + 16) + 16;
 }
 
 template <bool NEED_G, bool NEED_E>
 __device__ Tabs stage_tables(unsigned char* sm, const Args& a) {
   float* planes = reinterpret_cast<float*>(sm);
   float* dedx = planes + 129;
-  uint8_t* mat = reinterpret_cast<uint8_t*>(dedx + 4);
-  float2* tot = reinterpret_cast<float2*>(mat + 128 + 12);  // 16-byte aligned: 516+16+128+12 = 672
+  float* x0 = dedx + 4;
+  uint8_t* mat = reinterpret_cast<uint8_t*>(x0 + 4);
+  float2* tot = reinterpret_cast<float2*>(mat + 128 + 12);  // 16-byte aligned: 516+32+128+12 = 688
   float2* brem = tot + a.n_mat * NBINS;
   float4* cp = reinterpret_cast<float4*>(brem + a.n_mat * NBINS);
   for (int i = threadIdx.x; i <= (int)a.n_slabs; i += blockDim.x) planes[i] = a.planes[i];
   for (int i = threadIdx.x; i < (int)a.n_slabs; i += blockDim.x) mat[i] = a.mat[i];
-  if (threadIdx.x < 4) dedx[threadIdx.x] = a.dedx[threadIdx.x];
+  if (threadIdx.x < 4) {
+    dedx[threadIdx.x] = a.dedx[threadIdx.x];
+    x0[threadIdx.x] = a.x0[threadIdx.x];
+  }
   const int nt = (int)a.n_mat * NBINS;
   if (NEED_G) {
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
@@ -66,7 +70,9 @@ __device__ Tabs stage_tables(unsigned char* sm, const Args& a) {
   tb.cp = cp;
   tb.brem = brem;
   tb.dedx = dedx;
+  tb.x0 = x0;
   tb.n_slabs = (int)a.n_slabs;
+  tb.msc = a.msc;
   return tb;
 }
 
@@ -529,7 +535,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
       do_int = act;
       if (act) q_get(wq.q, QCAP, (wq.head + lane) % QCAP, t, cx, s2);
     }
-    if (do_int) interact<MODE>(type, t, cx, a.seed_lo, o);
+    if (do_int) interact<MODE>(type, t, cx, a.seed_lo, o, a.msc != 0);
     if (!once) __syncwarp();  // entries consumed before their ring slots are reused
     finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, s2, tl);
     if (!once) {
@@ -708,7 +714,7 @@ __global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_interact(const __grid_co
     uint32_t slot = 0;
     if (act) {
       q_get(queue_of<TYPE>(a, k), (size_t)a.cap, p, t, cx, slot);
-      interact<MODE>(TYPE, t, cx, a.seed_lo, o);
+      interact<MODE>(TYPE, t, cx, a.seed_lo, o, a.msc != 0);
     }
     finish<L, false, DENSE>(a, TYPE, it, lane, act, t, o, slot, tl);
   }
@@ -739,6 +745,45 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
                     (a.hybrid_t != 0 && left < a.hybrid_t);
   c->done = stop ? 1u : 0u;
   if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+#endif
+
+#ifdef ET_HOST_TU
+// ---- serving: collect the events completed since the last collection ----
+// One block.  For at most max_out completions after *cursor (the completion ring is
+// final: every iteration before this kernel has ended), copies the event's per-slab
+// deposits and its ledger to out_rows[j] ([n_slabs + 5] doubles) and its number to
+// out_events[j], clears the event's scores, ledger and live count (its number can be
+// given to a new event afterwards), advances the cursor and writes the count to
+// out_events[max_out].
+__global__ void k_serve_collect(const __grid_constant__ Args a, uint32_t* cursor,
+                                uint32_t* out_events, double* out_rows, uint32_t max_out) {
+  const uint32_t cur = *cursor;
+  const uint32_t done = *(volatile uint32_t*)&a.ctl->n_done;
+  const uint32_t n = done - cur < max_out ? done - cur : max_out;
+  const uint32_t ns = a.n_slabs, row = ns + 5u;
+  for (uint32_t j = 0; j < n; ++j) {
+    const uint32_t e = a.done_ring[(cur + j) % a.done_cap];
+    double* sc = a.score + (size_t)e * ns;
+    double* lg = a.ledger + (size_t)e * 5u;
+    for (uint32_t i = threadIdx.x; i < row; i += blockDim.x) {
+      if (i < ns) {
+        out_rows[(size_t)j * row + i] = sc[i];
+        sc[i] = 0.0;
+      } else {
+        out_rows[(size_t)j * row + i] = lg[i - ns];
+        lg[i - ns] = 0.0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      out_events[j] = e;
+      a.live[e] = 0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    *cursor = cur + n;
+    out_events[max_out] = n;
+  }
 }
 #endif
 

@@ -28,6 +28,12 @@ constexpr float TWO_MC2 = 0x1.05a1a8p+0f;   // 1.0219979 MeV
 constexpr float KC = 0x1.47ae14p-7f;        // 0.01 MeV, production and tracking cut
 constexpr float C_LIGHT = 0x1.2bcadep+8f;   // 299.792458 mm/ns
 constexpr float LOSS_FRAC = 0x1.99999ap-3f; // 0.2
+// toy model v2 (multiple scattering): step limit MSC_FR max(E / dEdx, MSC_RMIN), Highland
+// width 13.6 MeV / (beta c p) sqrt(x) (1 + 0.038 ln x)
+constexpr float MSC_FR = 0x1.47ae14p-5f;    // 0.04
+constexpr float MSC_RMIN = 0.5f;            // mm
+constexpr float HIGHLAND_E = 0x1.b33334p+3f; // 13.6 MeV
+constexpr float HIGHLAND_LOG = 0x1.374bc6p-5f; // 0.038
 constexpr float F_INF = __builtin_huge_valf();
 
 // Shared-memory copy of geometry and tables (block-local).
@@ -38,7 +44,9 @@ struct Tabs {
   const float4* cp;      // [n_mat][256] {Sigma_C, dC, Sigma_pair, dP}
   const float2* brem;    // [n_mat][256]
   const float* dedx;     // [n_mat]
+  const float* x0;       // [n_mat] radiation lengths (toy model v2)
   int n_slabs;
+  int msc;               // toy model v2: multiple scattering of e+-
 };
 
 // A secondary's id is derived when it is written: secondary_id(parent, step, ordinal).
@@ -132,6 +140,32 @@ __device__ __forceinline__ void rotate_about(float ux, float uy, float uz, float
   } else {
     nx = px; ny = py; nz = pz;
   }
+}
+
+// Toy model v2: the direction of a charged track that goes on after a step of length
+// s > 0 is turned by theta, phi (Philox block 66 of the step).  Highland's width at the
+// pre-step energy E and x = s / X0; 1 - cos(theta) = theta0^2 (-log u0) (small-angle
+// Gaussian law), clamped at cos(theta) = -1; phi = 2 pi u1; the Compton rotation.
+template <int MODE>
+__device__ __forceinline__ void msc_deflect(Trk& t, uint32_t pstep, uint32_t seed, float E,
+                                            float s, float x0) {
+  const float pbc = E * (E + TWO_MC2) / (E + MC2);  // beta c p
+  const float x = s / x0;
+  const float br = 1.0f + HIGHLAND_LOG * m_log<MODE>(x);
+  if (!(br > 0.0f)) return;
+  const float th0 = (HIGHLAND_E / pbc) * sqrtf(x) * br;
+  const uint4 r = philox((uint32_t)t.id, (uint32_t)(t.id >> 32), pstep, 66u, seed, t.event);
+  const float w = (th0 * th0) * (-m_log<MODE>(u01(r.x)));
+  float cost = 1.0f - w;
+  if (cost < -1.0f) cost = -1.0f;
+  const float sint = sqrtf((1.0f - cost) * (1.0f + cost));
+  float sphi, cphi;
+  m_sincos2pi<MODE>(u01(r.y), &sphi, &cphi);
+  float nx, ny, nz;
+  rotate_about(t.dx, t.dy, t.dz, sint * cphi, sint * sphi, cost, nx, ny, nz);
+  t.dx = nx;
+  t.dy = ny;
+  t.dz = nz;
 }
 
 // Positron at rest: two back-to-back photons of m_e c^2, isotropic (Philox block 65).
@@ -255,6 +289,11 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
       const float sl = num / dedx;
       if (sl < s) { s = sl; lim = LIM_LOSS; }
     }
+    if (tb.msc) {  // v2: multiple-scattering step limit
+      const float rng = E / dedx;
+      const float sm = MSC_FR * ((rng > MSC_RMIN) ? rng : MSC_RMIN);
+      if (sm < s) { s = sm; lim = LIM_MSC; }
+    }
   }
   if (sig > 0.0f && may_limit(t.nia, sig, s)) {
     const float s_phys = t.nia / sig;
@@ -314,7 +353,13 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
     o.alive = 0;
     o.death = DEATH_CUT;
     if (type == EP) annihilate<MODE>(o, t, pstep, seed);
-  } else if (lim == LIM_PHYS) {
+  } else {
+    // v2: the surviving charged track is deflected before any interaction
+    if (charged && tb.msc && s > 0.0f) {
+      msc_deflect<MODE>(t, pstep, seed, E, s, tb.x0[m]);
+      o.dirty |= D_DIR;
+    }
+    if (lim == LIM_PHYS) {
     cx.E = E;
     cx.sig = sig;
     if (!charged) {
@@ -326,6 +371,7 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
     cx.u2 = u01(r0.z);
     cx.u3 = u01(r0.w);
     return true;
+    }
   }
   balance(t, E, o);
   t.flags = (uint32_t)lim;
@@ -334,13 +380,15 @@ __device__ __forceinline__ bool transport(const int type, Trk& t, const Tabs& tb
 }
 
 // The discrete interaction that ends a PHYS-limited step, then the step's balance.
-// t is the post-transport state (its step counter not yet advanced); o is fresh.
+// t is the post-transport state (its step counter not yet advanced); o is fresh.  `msc`:
+// toy model v2, where the transport half has turned a charged track's direction.
 template <int MODE>
 __device__ __forceinline__ void interact(const int type, Trk& t, const Ctx& cx, uint32_t seed,
-                                         StepOut& o) {
+                                         StepOut& o, bool msc) {
   const bool charged = type != GAM;
   o.begin();
-  o.dirty = D_POS | D_NIA | D_STEP | D_TIME | D_LEN | D_FLAGS | (charged ? D_E : 0u);
+  o.dirty = D_POS | D_NIA | D_STEP | D_TIME | D_LEN | D_FLAGS | (charged ? D_E : 0u) |
+            (charged && msc ? D_DIR : 0u);
   o.slab_cont = t.slab;
   const uint32_t pstep = t.step;
   const float E = cx.E;
@@ -457,7 +505,7 @@ __device__ __forceinline__ void step_track(const int type, Trk& t, const Tabs& t
                                            float inv_dlog, float half, uint32_t seed, StepOut& o) {
   Ctx cx;
   if (transport<MODE>(type, t, tb, log_emin, inv_dlog, half, seed, o, cx))
-    interact<MODE>(type, t, cx, seed, o);
+    interact<MODE>(type, t, cx, seed, o, tb.msc != 0);
 }
 
 }  // namespace et

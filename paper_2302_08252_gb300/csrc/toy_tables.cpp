@@ -111,3 +111,9 @@ extern "C" et_status et_build_toy_tables(uint32_t n_materials, uint32_t n_nodes,
   if (inv_dlog_out) *inv_dlog_out = (float)((double)(n_nodes - 1) / std::log(1e8));
   return ET_OK;
 }
+
+extern "C" et_status et_toy_radiation_lengths(uint32_t n_materials, float* x0_out) {
+  if (n_materials < 1 || n_materials > 2 || !x0_out) return ET_ERR_INVALID;
+  for (uint32_t m = 0; m < n_materials; ++m) x0_out[m] = (float)kMedia[m].x0_mm;
+  return ET_OK;
+}

@@ -54,7 +54,7 @@ class et_config(C.Structure):
                 ("id_log_capacity", C.c_uint64), ("cuda_stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
                 ("serving", C.c_int32), ("reuse_slots", C.c_int32), ("hybrid_tracks", C.c_uint32),
-                ("split_interactions", C.c_int32)]
+                ("split_interactions", C.c_int32), ("msc", C.c_int32)]
 
 
 class et_iter_stats(C.Structure):
@@ -86,6 +86,8 @@ def _load():
         "et_create_geometry": ([vp, C.c_uint32, vp, vp, C.c_float], st),
         "et_load_tables": ([vp, C.c_uint32, C.c_uint32, C.c_float, C.c_float, vp, vp], st),
         "et_build_toy_tables": ([C.c_uint32, C.c_uint32, vp, vp, vp, vp], st),
+        "et_load_msc": ([vp, C.c_uint32, vp], st),
+        "et_toy_radiation_lengths": ([C.c_uint32, vp], st),
         "et_build_toy_tables_fp64": ([C.c_uint32, C.c_uint32, vp, vp, vp, vp], st),
         "et_run_fp64": ([C.c_uint32, vp, vp, C.c_double, C.c_uint32, C.c_double, C.c_double, vp,
                          vp, vp, C.c_size_t, C.c_uint64, C.c_uint32, C.c_uint32, vp, vp,
@@ -107,6 +109,12 @@ def _load():
         "et_restore": ([vp, vp, C.c_uint64], st),
         "et_poll_completed": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
         "et_release_event": ([vp, C.c_uint32], st),
+        "et_serve_submit": ([vp, vp, C.c_size_t, C.c_uint32, vp], st),
+        "et_serve_round": ([vp, C.c_uint32, vp, vp, C.c_uint64, C.POINTER(C.c_uint64),
+                            C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)], st),
+        "et_serve_flush": ([vp, vp, vp, C.c_uint64, C.POINTER(C.c_uint64),
+                            C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)], st),
+        "et_serve_capacity": ([vp, C.POINTER(C.c_uint32)], st),
         "et_set_timing": ([vp, C.c_int], st),
         "et_read_timing": ([vp, C.POINTER(C.c_double), C.POINTER(C.c_uint64)], st),
         "et_transport_noalloc": ([C.c_uint32, vp, vp, C.c_float, C.c_uint32, C.c_float, C.c_float,
@@ -170,7 +178,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
               driver=DRIVER_HOSTLOOP, block_size=256, seed=1, max_events=1, max_iters=1 << 16,
               instrument=False, id_log=False, id_log_capacity=0, stream=None,
               use_torch_allocator=True, serving=False, reuse_slots=False,
-              allocator=None, hybrid_tracks=0, split=False) -> Context:
+              allocator=None, hybrid_tracks=0, split=False, msc=False) -> Context:
     """Create a context.  stream: a torch.cuda.Stream, an int cudaStream_t, or None for
     torch's current stream.  allocator: optional (alloc(nbytes, stream) -> int address,
     free(address)) pair of Python callables for the library's device buffers; default
@@ -202,6 +210,7 @@ def et_create(capacity_log2=20, form=FORM_DENSE, layout=LAYOUT_AOS, mode=MODE_ST
     cfg.reuse_slots = int(bool(reuse_slots))
     cfg.hybrid_tracks = int(hybrid_tracks)
     cfg.split_interactions = int(bool(split))
+    cfg.msc = int(bool(msc))
     cbs = None
     if allocator is not None:
         fa, ff = allocator
@@ -247,6 +256,19 @@ def et_build_toy_tables(n_materials=2, n_nodes=257):
     if st != ET_OK:
         raise EtError(st, "et_build_toy_tables")
     return {"sigma": sig, "dedx": dedx, "log_emin": float(le[0]), "inv_dlog": float(idl[0])}
+
+
+def et_toy_radiation_lengths(n_materials=2) -> np.ndarray:
+    x0 = np.zeros(n_materials, dtype=np.float32)
+    st = lib.et_toy_radiation_lengths(n_materials, _p(x0))
+    if st != ET_OK:
+        raise EtError(st, "et_toy_radiation_lengths")
+    return x0
+
+
+def et_load_msc(ctx, x0_mm):
+    x0 = np.ascontiguousarray(x0_mm, dtype=np.float32)
+    _check(ctx, lib.et_load_msc(ctx.handle, len(x0), _p(x0)))
 
 
 def et_build_toy_tables_fp64(n_materials=2, n_nodes=257):
@@ -369,6 +391,46 @@ def et_poll_completed(ctx, cap=1 << 16):
 
 def et_release_event(ctx, event):
     _check(ctx, lib.et_release_event(ctx.handle, event))
+
+
+def et_serve_submit(ctx, primaries: np.ndarray, event: int, reserve):
+    """Queue one event's primaries for the native serving loop (see et.h)."""
+    p = np.ascontiguousarray(primaries)
+    assert p.dtype == PRIMARY_DTYPE
+    r = np.ascontiguousarray(reserve, dtype=np.uint32)
+    assert r.shape == (3,)
+    _check(ctx, lib.et_serve_submit(ctx.handle, _p(p), len(p), int(event), _p(r)))
+
+
+class ServeBuffers:
+    """Host result buffers of the serving loop: events and [n_slabs + 5] rows."""
+
+    def __init__(self, ctx, n_slabs: int):
+        m = C.c_uint32()
+        _check(ctx, lib.et_serve_capacity(ctx.handle, C.byref(m)))
+        self.cap = m.value
+        self.events = np.zeros(self.cap, dtype=np.uint32)
+        self.rows = np.zeros((self.cap, n_slabs + 5), dtype=np.float64)
+
+
+def _serve_out(buf, n, steps, inflight):
+    k = int(n.value)
+    return (buf.events[:k].copy(), buf.rows[:k].copy(), int(steps.value), int(inflight.value))
+
+
+def et_serve_round(ctx, buf: ServeBuffers, iters: int):
+    """One round; returns (events, rows, steps, in_flight) of the previous round."""
+    n, steps, inflight = C.c_uint64(), C.c_uint64(), C.c_uint32()
+    _check(ctx, lib.et_serve_round(ctx.handle, int(iters), _p(buf.events), _p(buf.rows), buf.cap,
+                                   C.byref(n), C.byref(steps), C.byref(inflight)))
+    return _serve_out(buf, n, steps, inflight)
+
+
+def et_serve_flush(ctx, buf: ServeBuffers):
+    n, steps, inflight = C.c_uint64(), C.c_uint64(), C.c_uint32()
+    _check(ctx, lib.et_serve_flush(ctx.handle, _p(buf.events), _p(buf.rows), buf.cap,
+                                   C.byref(n), C.byref(steps), C.byref(inflight)))
+    return _serve_out(buf, n, steps, inflight)
 
 
 def et_set_timing(ctx, on=True):
@@ -498,11 +560,14 @@ def et_run_fp64(geom, tables64, primaries: np.ndarray, seed, n_events, capacity_
 
 
 def make_context(geom: dict, max_events: int, tables: dict | None = None, **kw) -> Context:
-    """Create a context and load the calorimeter and the toy tables (convenience)."""
+    """Create a context and load the calorimeter and the toy tables (convenience); with
+    msc=True also the toy radiation lengths (toy model v2)."""
     ctx = et_create(max_events=max_events, **kw)
     et_create_geometry(ctx, geom["thickness"], geom["material"], geom["half_xy"])
     t = tables if tables is not None else et_build_toy_tables()
     et_load_tables(ctx, t["sigma"], t["dedx"], t["log_emin"], t["inv_dlog"])
+    if kw.get("msc"):
+        et_load_msc(ctx, et_toy_radiation_lengths(len(t["dedx"])))
     return ctx
 
 

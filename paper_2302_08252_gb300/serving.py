@@ -1,19 +1,22 @@
 """Continuous batching of shower events over the C ABI (the serving pattern).
 
 Events arrive as a Geant4 offload hook would hand them over (each a set of primaries,
-at an arrival time).  The server keeps a single transport context on the GPU and loops:
+at an arrival time).  The server keeps one transport context on the GPU and drives the
+library's native serving loop (et_serve_submit / et_serve_round, include/et.h):
 
-  1. admit waiting events whose arrival time has passed while their estimated track
-     footprint fits the free track-buffer capacity (admission by memory), injecting all
-     newly admitted events with one call;
-  2. run a few transport iterations (the showers already in flight keep going, the new
-     ones start: their work overlaps on the device);
-  3. collect the events whose last track died (device-side live-track counters), read
-     their per-layer deposits and ledgers, release their event numbers.
+  1. every arrived event is submitted with its reserve (estimated peak track slots per
+     type); the library admits queued events in order while their reserves fit the free
+     track-buffer capacity (admission by memory) and injects them;
+  2. each round runs a few transport iterations with every shower in flight (new ones
+     start while the others go on: their work overlaps on the device), and a device
+     kernel collects the events whose last track died (device-side live-track counters)
+     -- their per-layer deposits and ledgers -- into one buffer copied to pinned memory;
+  3. a round returns the completions of the round before it: the GPU is already running
+     the next round while the host admits and reads back.
 
-Latency is arrival -> results read on the host.  Every random draw is keyed by the
-event number and the track's own step count, so an event's history does not depend on
-when it was admitted or what else was in flight.
+Latency is arrival -> results on the host.  Every random draw is keyed by the event
+number and the track's own step count, so an event's history does not depend on when it
+was admitted or what else was in flight.
 """
 from __future__ import annotations
 
@@ -60,8 +63,12 @@ class ServeStats:
     max_inflight: int = 0
     rounds: int = 0
 
-    def latency_quantiles(self, qs=(0.5, 0.99)):
-        lat = np.array([r.latency for r in self.results])
+    def latency_quantiles(self, qs=(0.5, 0.99), skip_frac: float = 0.1):
+        """Latency quantiles over the events after the first skip_frac of the stream (by
+        arrival): the warm-up, while the device fills, is left out."""
+        res = sorted(self.results, key=lambda r: r.arrival)
+        res = res[int(len(res) * skip_frac):] or res
+        lat = np.array([r.latency for r in res])
         return {f"p{int(q * 100)}": float(np.quantile(lat, q)) for q in qs}
 
 
@@ -84,47 +91,48 @@ class Server:
                                    form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
                                    layout=layout, driver=driver, seed=seed, serving=True,
                                    reuse_slots=(form == "sparse"))
+        self.buf = et.ServeBuffers(self.ctx, self.n_slabs)
+
+    def _collect(self, out, stats, submitted, t_done):
+        events, rows, steps, inflight = out
+        stats.steps += steps
+        ns = self.n_slabs
+        for e, row in zip(events, rows):
+            r, t_sub = submitted.pop(int(e))
+            score = row[:ns].copy()
+            lg = row[ns:]
+            ledger = {"injected": float(lg[0]), "below_cut": float(lg[1]),
+                      "escaped": float(lg[2]), "mass_created": float(lg[3]),
+                      "mass_consumed": float(lg[4]),
+                      "deposited_cont": float(score.sum() - lg[1])}
+            stats.results.append(Result(int(e), r.arrival, t_sub, t_done, score, ledger))
+        stats.max_inflight = max(stats.max_inflight, inflight)
 
     def serve(self, requests: list[Request], realtime: bool = True) -> ServeStats:
         """Serve the requests (sorted by arrival).  realtime: arrivals follow the wall
         clock; otherwise every request is available at once (throughput mode)."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        inflight: dict[int, tuple[Request, float, np.ndarray]] = {}
-        reserved = np.zeros(3)
+        submitted: dict[int, tuple[Request, float]] = {}
         stats = ServeStats()
         t0 = time.perf_counter()
         now = lambda: time.perf_counter() - t0
-        while pending or inflight:
+        while pending or submitted:
             t = now()
-            batch = []
             while pending and (not realtime or pending[0].arrival <= t):
-                r = pending[0]
-                need = reserve(r.primaries)
-                if inflight and np.any(reserved + need > 0.9 * self.capacity):
-                    break  # wait until memory frees up
-                if r.event in inflight:
+                r = pending.popleft()
+                if r.event in submitted:  # its number is still in use: wait for it
+                    pending.appendleft(r)
                     break
-                pending.popleft()
-                reserved += need
-                inflight[r.event] = (r, t, need)
-                batch.append(r.primaries)
-            if batch:
-                et.et_inject(self.ctx, np.concatenate(batch))
-            stats.max_inflight = max(stats.max_inflight, len(inflight))
-            if not inflight:
+                et.et_serve_submit(self.ctx, r.primaries, r.event,
+                                   reserve(r.primaries).astype(np.uint32))
+                submitted[r.event] = (r, t)
+            if not submitted:
                 if pending:  # idle until the next arrival
                     time.sleep(max(0.0, pending[0].arrival - now()))
                 continue
-            tot = et.et_run_until_empty(self.ctx, self.iters)
-            stats.steps += tot["steps"]
+            out = et.et_serve_round(self.ctx, self.buf, self.iters)
             stats.rounds += 1
-            for e in et.et_poll_completed(self.ctx):
-                e = int(e)
-                r, t_adm, need = inflight.pop(e)
-                score, ledger = et.et_read_scoring(self.ctx, e, self.n_slabs)
-                stats.results.append(Result(e, r.arrival, t_adm, now(), score, ledger))
-                et.et_release_event(self.ctx, e)
-                reserved -= need
+            self._collect(out, stats, submitted, now())
         stats.wall = now()
         return stats
 

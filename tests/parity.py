@@ -38,9 +38,10 @@ def run_gpu(geom, primaries, n_events, form="dense", layout="aos", driver="hostl
     return out
 
 
-def oracle_run(geom, primaries, n_events, idlog=True, nthreads=8, mode=oracle.STRICT_FP32):
+def oracle_run(geom, primaries, n_events, idlog=True, nthreads=8, mode=oracle.STRICT_FP32,
+               msc=False):
     return oracle.run(geom, primaries, n_events=n_events, seed=1, idlog=idlog, nthreads=nthreads,
-                      mode=mode)
+                      mode=mode, msc=msc)
 
 
 def sorted_records(log):

@@ -1,8 +1,11 @@
-"""Serving with continuous batching: events that arrive while others are on the GPU are
-admitted as memory frees up, their work overlaps, and each event's result is the same
-as when it runs alone (strict mode: the same per-step deposits, summed in another order,
-so within the parity tolerance), for the dense form and for the sparse form with slot
-reuse."""
+"""Serving with continuous batching through the library's native loop (et_serve_*):
+events that arrive while others are on the GPU are admitted as memory frees up, their
+work overlaps, and each event's result is the same as when it runs alone -- strict mode,
+the same per-step deposits summed in another order, so within the parity tolerance --
+for the dense form and for the sparse form with slot reuse.  Events are of realistic
+size (100-160 mixed primaries each).  The serving run's total step count equals the sum
+of the events' step counts alone (bit-exact), admission never overflows the buffers
+(the status word stays clear), and a few events also match the oracle."""
 import numpy as np
 import pytest
 
@@ -13,29 +16,67 @@ from parity import DEPOSIT_RTOL, oracle_run, run_gpu
 pytestmark = pytest.mark.gpu
 
 
+def _requests(n_events, rate, seed=5):
+    """n_events events of 100-160 mixed primaries (energies capped at 2 GeV), Poisson
+    arrivals at `rate` per second."""
+    from paper_2302_08252_gb300 import serving
+    sizes = 100 + (np.arange(n_events) * 37) % 61
+    p = W.mixed_primaries(int(sizes.sum()), seed=seed)
+    p["ekin"] = np.minimum(p["ekin"], np.float32(2000.0))
+    p["event"] = np.repeat(np.arange(n_events, dtype=np.uint32), sizes)
+    p = W.assign_ids(p)
+    t = W.poisson_arrivals(rate, n_events, seed=W.ARRIVAL_SEED)
+    return [serving.Request(i, float(t[i]), p[p["event"] == i]) for i in range(n_events)]
+
+
+def _close(a, b):
+    return np.all(np.abs(a - b) <= DEPOSIT_RTOL * np.abs(b) + 1e-9)
+
+
 @pytest.mark.parametrize("form", ["dense", "sparse"])
 def test_each_event_same_alone_and_in_the_mix(geom, form):
-    from paper_2302_08252_gb300 import serving
-    reqs = serving.poisson_requests(rate=3000.0, n_events=48, max_primaries=4)
-    srv = serving.Server(geom, form=form, layout="aos", driver="persistent", capacity_log2=20,
-                         max_events=64, iters_per_round=4)
+    from paper_2302_08252_gb300 import et, serving
+    n_ev = 40
+    reqs = _requests(n_ev, rate=2000.0)
+    srv = serving.Server(geom, form=form, layout="aosoa32" if form == "dense" else "aos",
+                         driver="persistent", capacity_log2=20, max_events=64, iters_per_round=8)
     st = srv.serve(reqs, realtime=True)
-    assert len(st.results) == len(reqs)
+    assert len(st.results) == n_ev and sorted(r.event for r in st.results) == list(range(n_ev))
     assert st.max_inflight > 1          # requests overlapped on the device
+    assert et.et_read_counters(srv.ctx)["status"] == 0   # no buffer ever overflowed
     by_event = {r.event: r for r in st.results}
-    for req in reqs[:12]:
+    steps_alone = 0
+    for req in reqs:
         alone = run_gpu(geom, req.primaries, 64, form="dense", layout="aos", driver="hostloop",
-                        id_log=False, capacity_log2=18)
-        ref = alone["score"][req.event]
-        got = by_event[req.event].score
-        assert np.all(np.abs(got - ref) <= DEPOSIT_RTOL * np.abs(ref) + 1e-9)
-        assert by_event[req.event].ledger["injected"] == alone["ledger"][req.event, 0]
+                        id_log=False, capacity_log2=19)
+        steps_alone += sum(alone["counters"]["steps"])
+        got = by_event[req.event]
+        assert _close(got.score, alone["score"][req.event]), req.event
+        a = alone["ledger"][req.event]
+        assert got.ledger["injected"] == a[0]
+        for k, name in ((2, "below_cut"), (3, "escaped"), (4, "mass_created"),
+                        (5, "mass_consumed")):
+            assert got.ledger[name] == pytest.approx(a[k], rel=1e-9, abs=1e-9), (req.event, name)
+    assert st.steps == steps_alone      # the same histories, step for step
     # and against the oracle for a few
     for req in reqs[:4]:
-        o = oracle_run(geom, req.primaries, 64, idlog=False)
-        ref = o["score"][req.event]
-        got = by_event[req.event].score
-        assert np.all(np.abs(got - ref) <= DEPOSIT_RTOL * np.abs(ref) + 1e-9)
+        o = oracle_run(geom, req.primaries, 64, idlog=False, nthreads=16)
+        assert _close(by_event[req.event].score, o["score"][req.event])
+
+
+def test_serving_admission_waits_for_memory(geom):
+    """A capacity that holds only a few events' reserves: admission waits for completions,
+    every event is served, and nothing overflows."""
+    from paper_2302_08252_gb300 import et, serving
+    reqs = _requests(24, rate=1e6, seed=6)           # all arrive at once
+    srv = serving.Server(geom, form="dense", layout="aosoa32", driver="persistent",
+                         capacity_log2=16, max_events=32, iters_per_round=8)
+    need = [int(serving.reserve(r.primaries).max()) for r in reqs]
+    assert max(need) < 0.9 * (1 << 16) < sum(need)  # they cannot all be in flight at once
+    st = srv.serve(reqs, realtime=False)
+    assert sorted(r.event for r in st.results) == list(range(24))
+    assert et.et_read_counters(srv.ctx)["status"] == 0
+    assert st.max_inflight >= 2
 
 
 def test_sparse_slot_reuse_keeps_slots_bounded(geom):
