@@ -334,7 +334,8 @@ def serving_measure(geom, args):
         q = st.latency_quantiles()
         out[name] = {"form": form, "layout": layout, "driver": driver,
                      "p50_ms": 1e3 * q["p50"], "p99_ms": 1e3 * q["p99"],
-                     "steps_per_s": st.steps / st.wall, "wall_s": st.wall,
+                     "steps_per_s": st.steps / st.wall, "steady_steps_per_s": st.steady_rate(),
+                     "wall_s": st.wall,
                      "max_inflight": st.max_inflight, "rounds": st.rounds,
                      "latency_events": len(st.results) - int(0.1 * len(st.results))}
         del srv

@@ -57,6 +57,7 @@ struct ServeState {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   uint64_t issued = 0, delivered = 0;          // rounds
   uint64_t steps_seen = 0;                     // cumulative steps at the last delivery
+  uint64_t last_pop = 0;                       // active tracks at the last delivered round's end
   std::vector<Primary> batch;
 };
 
@@ -1362,6 +1363,8 @@ static et_status serve_deliver(et_ctx* c, ServeState* s, uint64_t k, uint32_t* e
   const uint64_t all = d.steps[0] + d.steps[1] + d.steps[2];
   if (steps) *steps += all - s->steps_seen;
   s->steps_seen = all;
+  const uint32_t* cur = d.cnt[d.iter % 3];
+  s->last_pop = (uint64_t)cur[cw(EM)] + cur[cw(EP)] + cur[cw(GAM)];
   s->delivered = k + 1;
   return ET_OK;
 }
@@ -1393,9 +1396,25 @@ et_status et_serve_round(et_ctx* c, uint32_t iters, uint32_t* events, double* ro
     st = et_inject(c, reinterpret_cast<const et_primary*>(s->batch.data()), s->batch.size());
     if (st != ET_OK) return st;
   }
-  // 2. the round's iterations: the persistent kernel stops after `iters` of them
-  if (iters > 0 && !s->inflight.empty()) {
-    if (c->cfg.driver == ET_DRIVER_PERSISTENT) {
+  // 2. the round's iterations: the persistent kernel stops after `iters` of them; with
+  // the hybrid driver, a round whose stream was last seen at or above the switch-over
+  // population runs the graph of per-type step kernels instead (both stop where the
+  // population crosses it, after at least one iteration)
+  const bool hybrid = c->cfg.driver == ET_DRIVER_HYBRID;
+  if (iters > 0 && !s->inflight.empty() && hybrid && s->last_pop >= c->args.hybrid_t) {
+    void* pr[] = {(void*)&c->args, (void*)&iters};
+    st = launch(c, (const void*)k_round_stop, 1, 1, 0, pr);
+    if (st != ET_OK) return st;
+    if (!c->gexec) {
+      st = build_graph(c);
+      if (st != ET_OK) return st;
+    }
+    EventPair* ev = timing_begin(c);
+    CUDA_TRY(c, cudaGraphLaunch(c->gexec, c->stream));
+    timing_end(c, ev);
+    c->launches += 1;
+  } else if (iters > 0 && !s->inflight.empty()) {
+    if (c->cfg.driver == ET_DRIVER_PERSISTENT || hybrid) {
       s->h_rel[k % 2][0] = iters;
       CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->stop_rel, s->h_rel[k % 2], 4, cudaMemcpyHostToDevice,
                                   c->stream));

@@ -749,6 +749,13 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
 #endif
 
 #ifdef ET_HOST_TU
+// ---- serving: the graph driver's iteration limit, relative to where the stream is ----
+__global__ void k_round_stop(const __grid_constant__ Args a, uint32_t rel) {
+  DevCtl* c = a.ctl;
+  const uint32_t it = c->iter;
+  c->stop_iter = it + rel < it ? 0xffffffffu : it + rel;
+}
+
 // ---- serving: collect the events completed since the last collection ----
 // One block.  For at most max_out completions after *cursor (the completion ring is
 // final: every iteration before this kernel has ended), copies the event's per-slab

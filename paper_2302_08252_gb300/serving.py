@@ -62,6 +62,19 @@ class ServeStats:
     wall: float = 0.0
     max_inflight: int = 0
     rounds: int = 0
+    timeline: list = field(default_factory=list)  # (time, steps so far, completions so far)
+
+    def steady_rate(self, lo: float = 0.1, hi: float = 0.9) -> float:
+        """Track-steps per second between the rounds that returned the lo and hi fractions
+        of the completions: the sustained rate without the start-up and the final drain."""
+        n = len(self.results)
+        if n < 10 or len(self.timeline) < 3:
+            return self.steps / max(self.wall, 1e-9)
+        t = [x for x in self.timeline if x[2] >= lo * n]
+        u = [x for x in self.timeline if x[2] >= hi * n]
+        if not t or not u or u[0][0] <= t[0][0]:
+            return self.steps / max(self.wall, 1e-9)
+        return (u[0][1] - t[0][1]) / (u[0][0] - t[0][0])
 
     def latency_quantiles(self, qs=(0.5, 0.99), skip_frac: float = 0.1):
         """Latency quantiles over the events after the first skip_frac of the stream (by
@@ -132,7 +145,9 @@ class Server:
                 continue
             out = et.et_serve_round(self.ctx, self.buf, self.iters)
             stats.rounds += 1
-            self._collect(out, stats, submitted, now())
+            t_done = now()
+            self._collect(out, stats, submitted, t_done)
+            stats.timeline.append((t_done, stats.steps, len(stats.results)))
         stats.wall = now()
         return stats
 

@@ -43,7 +43,8 @@ def run(rate: float, n_events: int, max_primaries: int, warmup_frac: float, form
             "offered_gev_per_s": gev / max(1e-9, reqs[-1].arrival),
             "p50_ms": 1e3 * float(np.quantile(lat, 0.5)),
             "p99_ms": 1e3 * float(np.quantile(lat, 0.99)),
-            "steps_per_s": st.steps / st.wall, "wall_s": st.wall,
+            "steps_per_s": st.steps / st.wall, "steady_steps_per_s": st.steady_rate(),
+            "wall_s": st.wall,
             "max_inflight": st.max_inflight, "rounds": st.rounds,
             "latency_events": int(len(lat))}
 
