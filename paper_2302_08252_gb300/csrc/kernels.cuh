@@ -467,15 +467,26 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
       }
     }
   }
-  // serving: live-track count of the event; the step that brings it to zero ends the event
-  if (a.live && act) {
-    const int delta = (o.alive ? 1 : 0) + nsec - 1;
-    if (delta != 0) {
-      const int old = atomicAdd(&a.live[t.event], delta);
-      if (old + delta == 0) {
-        const uint32_t pos = atomicAdd(&ctl->n_done, 1u);
-        a.done_ring[pos % a.done_cap] = t.event;
+  // serving: live-track count of the event; the update that brings it to zero ends the
+  // event.  The warp's lanes of one event add their changes first (a ballot per event, an
+  // integer warp reduction), so each event of the warp takes one atomic: a few events in
+  // flight would otherwise see one atomic per lane on a handful of counters.
+  if (a.live) {
+    const int delta = act ? (o.alive ? 1 : 0) + nsec - 1 : 0;
+    uint32_t pend = __ballot_sync(FULL, delta != 0);
+    while (pend) {
+      const int src = __ffs(pend) - 1;
+      const uint32_t ev = __shfl_sync(FULL, t.event, src);
+      const uint32_t grp = __ballot_sync(FULL, delta != 0 && t.event == ev) & pend;
+      const int sum = __reduce_add_sync(FULL, ((grp >> lane) & 1u) ? delta : 0);
+      if ((int)lane == src && sum != 0) {
+        const int old = atomicAdd(&a.live[ev], sum);
+        if (old + sum == 0) {
+          const uint32_t pos = atomicAdd(&ctl->n_done, 1u);
+          a.done_ring[pos % a.done_cap] = ev;
+        }
       }
+      pend &= ~grp;
     }
   }
 }
