@@ -163,6 +163,7 @@ struct Args {
   // the completion ring (NULL: off)
   int32_t* live;                // [max_events]
   uint32_t* done_ring;          // [done_cap] completed event ids, position n_done % done_cap
+  uint32_t* ev_flag;            // [max_events] 1: injected, completion not yet reported
   uint32_t done_cap;
   // sparse form with slot reuse: ring of freed slots per type (NULL: slots never reused)
   uint32_t* free_ring[NTYPES];  // [cap] each

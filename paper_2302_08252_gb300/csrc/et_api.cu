@@ -208,6 +208,13 @@ static et_status launch(et_ctx* c, const void* fn, int grid, int block, size_t s
   return ET_OK;
 }
 
+// Serving: append the events that have ended since the last scan to the completion ring.
+static et_status scan_done(et_ctx* c) {
+  void* params[] = {(void*)&c->args};
+  const int grid = (int)((c->cfg.max_events + 255u) / 256u);
+  return launch(c, (const void*)k_scan_done, grid < 152 ? grid : 152, 256, 0, params);
+}
+
 // One thread per input: the primitives exactly as the step kernels use them.
 __global__ void k_debug_eval(int what, const void* in, void* out, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,8 +316,9 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
   if (k.serving) {
     a.live = (int32_t*)dalloc(c, (size_t)k.max_events * 4u);
     a.done_ring = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
+    a.ev_flag = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
     a.done_cap = k.max_events;
-    if (!a.live || !a.done_ring) return fail(c, ET_ERR_NOMEM, "serving counters");
+    if (!a.live || !a.done_ring || !a.ev_flag) return fail(c, ET_ERR_NOMEM, "serving counters");
   }
   if (k.reuse_slots && !c->dense) {
     for (int t = 0; t < 3; ++t) {
@@ -368,7 +376,10 @@ et_status et_reset(et_ctx* c) {
   if (a.score)
     CUDA_TRY(c, cudaMemsetAsync(a.score, 0, (size_t)a.max_events * a.n_slabs * 8u, c->stream));
   if (a.trace) CUDA_TRY(c, cudaMemsetAsync(a.trace, 0, 3u * NLEAF * 2u * 8u, c->stream));
-  if (a.live) CUDA_TRY(c, cudaMemsetAsync(a.live, 0, (size_t)a.max_events * 4u, c->stream));
+  if (a.live) {
+    CUDA_TRY(c, cudaMemsetAsync(a.live, 0, (size_t)a.max_events * 4u, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(a.ev_flag, 0, (size_t)a.max_events * 4u, c->stream));
+  }
   c->done_read = 0;
   for (int t = 0; t < 3; ++t)
     for (int h = 0; h < 2; ++h)
@@ -983,7 +994,9 @@ et_status et_read_counters(et_ctx* c, et_counters* out) {
 et_status et_poll_completed(et_ctx* c, uint32_t* events, uint64_t cap, uint64_t* n) {
   if (!c || !n) return ET_ERR_INVALID;
   if (!c->args.live) return fail(c, ET_ERR_STATE, "not a serving context");
-  et_status s = sync_ctl(c);
+  et_status s = scan_done(c);
+  if (s != ET_OK) return s;
+  s = sync_ctl(c);
   if (s != ET_OK) return s;
   const uint32_t done = c->h_ctl->n_done;
   uint32_t avail = done - c->done_read;
@@ -1012,7 +1025,10 @@ et_status et_release_event(et_ctx* c, uint32_t event) {
   const size_t ns = c->args.n_slabs;
   CUDA_TRY(c, cudaMemsetAsync(c->args.score + (size_t)event * ns, 0, ns * 8u, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->args.ledger + (size_t)event * 5u, 0, 5u * 8u, c->stream));
-  if (c->args.live) CUDA_TRY(c, cudaMemsetAsync(c->args.live + event, 0, 4u, c->stream));
+  if (c->args.live) {
+    CUDA_TRY(c, cudaMemsetAsync(c->args.live + event, 0, 4u, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->args.ev_flag + event, 0, 4u, c->stream));
+  }
   return ET_OK;
 }
 
@@ -1098,7 +1114,7 @@ struct SnapSection {
   uint64_t bytes;
 };
 enum : uint32_t { SN_CTL = 1, SN_TRK, SN_IDX, SN_FREE, SN_SCORE, SN_LEDGER, SN_COUNTS, SN_LIVE,
-                  SN_DONE, SN_IDLOG, SN_TRACE, SN_HEAT };
+                  SN_DONE, SN_IDLOG, SN_TRACE, SN_HEAT, SN_EVFLAG };
 constexpr char kSnapMagic[8] = {'E', 'T', 'S', 'N', 'A', 'P', '1', 0};
 
 struct SnapItem {
@@ -1142,6 +1158,7 @@ static std::vector<SnapItem> snapshot_items(et_ctx* c) {
   if (a.live) {
     v.push_back({SN_LIVE, 0, a.live, (uint64_t)a.max_events * 4u});
     v.push_back({SN_DONE, 0, a.done_ring, (uint64_t)a.done_cap * 4u});
+    v.push_back({SN_EVFLAG, 0, a.ev_flag, (uint64_t)a.max_events * 4u});
   }
   if (a.idlog) {
     const uint64_t m = std::min<uint64_t>(h.idlog_n, a.idlog_cap);
@@ -1251,6 +1268,7 @@ et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
       case SN_COUNTS: dev = a.counts_log; limit = (uint64_t)a.max_iters * 12u; break;
       case SN_LIVE: dev = a.live; limit = (uint64_t)a.max_events * 4u; break;
       case SN_DONE: dev = a.done_ring; limit = (uint64_t)a.done_cap * 4u; break;
+      case SN_EVFLAG: dev = a.ev_flag; limit = (uint64_t)a.max_events * 4u; break;
       case SN_IDLOG: dev = a.idlog; limit = a.idlog_cap * sizeof(IdRec); break;
       case SN_TRACE: dev = a.trace; limit = 3u * NLEAF * 2u * 8u; break;
       default: break;
@@ -1435,6 +1453,8 @@ et_status et_serve_round(et_ctx* c, uint32_t iters, uint32_t* events, double* ro
     }
   }
   // 3. collect the completed events, copy them and the counters to pinned host memory
+  st = scan_done(c);
+  if (st != ET_OK) return st;
   {
     void* params[] = {(void*)&c->args, (void*)&s->d_cursor, (void*)&s->d_events,
                       (void*)&s->d_rows, (void*)&s->max_out};

@@ -467,10 +467,11 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
       }
     }
   }
-  // serving: live-track count of the event; the update that brings it to zero ends the
-  // event.  The warp's lanes of one event add their changes first (a ballot per event, an
-  // integer warp reduction), so each event of the warp takes one atomic: a few events in
-  // flight would otherwise see one atomic per lane on a handful of counters.
+  // serving: live-track count of the event (an event whose count is back to zero has
+  // ended; k_scan_done reports it between launches).  The warp's lanes of one event add
+  // their changes first (a ballot per event, an integer warp reduction), and the sum goes
+  // out as a reduction that nothing waits for: a few events in flight would otherwise see
+  // one atomic round trip per lane on a handful of counters.
   if (a.live) {
     const int delta = act ? (o.alive ? 1 : 0) + nsec - 1 : 0;
     uint32_t pend = __ballot_sync(FULL, delta != 0);
@@ -479,13 +480,8 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
       const uint32_t ev = __shfl_sync(FULL, t.event, src);
       const uint32_t grp = __ballot_sync(FULL, delta != 0 && t.event == ev) & pend;
       const int sum = __reduce_add_sync(FULL, ((grp >> lane) & 1u) ? delta : 0);
-      if ((int)lane == src && sum != 0) {
-        const int old = atomicAdd(&a.live[ev], sum);
-        if (old + sum == 0) {
-          const uint32_t pos = atomicAdd(&ctl->n_done, 1u);
-          a.done_ring[pos % a.done_cap] = ev;
-        }
-      }
+      if ((int)lane == src && sum != 0)
+        asm volatile("red.global.add.s32 [%0], %1;" ::"l"(a.live + ev), "r"(sum) : "memory");
       pend &= ~grp;
     }
   }
@@ -760,6 +756,20 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
 #endif
 
 #ifdef ET_HOST_TU
+// ---- serving: report the events whose last track has died ----
+// Between launches (every step has been counted): an event that was injected and whose
+// live-track count is back to zero is appended to the completion ring, once.
+__global__ void k_scan_done(const __grid_constant__ Args a) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < a.max_events;
+       e += gridDim.x * blockDim.x) {
+    if (a.ev_flag[e] != 0u && a.live[e] == 0) {
+      a.ev_flag[e] = 0u;
+      const uint32_t pos = atomicAdd(&a.ctl->n_done, 1u);
+      a.done_ring[pos % a.done_cap] = e;
+    }
+  }
+}
+
 // ---- serving: the graph driver's iteration limit, relative to where the stream is ----
 __global__ void k_round_stop(const __grid_constant__ Args a, uint32_t rel) {
   DevCtl* c = a.ctl;
@@ -1062,7 +1072,10 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
     t.len = 0.0f;
     t.flags = 0;
     atomicAdd(&a.ledger[(size_t)t.event * 5 + 0], (double)t.e);
-    if (a.live) atomicAdd(&a.live[t.event], 1);
+    if (a.live) {
+      atomicAdd(&a.live[t.event], 1);
+      a.ev_flag[t.event] = 1u;
+    }
   }
   const uint32_t packed = ok ? (1u << (10 * type)) : 0u;
   uint32_t q0, q1, q2;
