@@ -90,8 +90,8 @@ typedef struct {
   et_alloc_fn alloc;        /* optional; both or neither */
   et_free_fn free;
   void* alloc_user;
-  int32_t serving;          /* 1: count live tracks per event and report completed events
-                               (et_poll_completed), for continuous batching; the iteration
+  int32_t serving;          /* 1: report completed events (et_poll_completed, the et_serve_*
+                               loop), for continuous batching; the iteration
                                count log then wraps (iteration it at entry it % max_iters)
                                instead of filling up */
   int32_t reuse_slots;      /* sparse form: 1 = slots of dead tracks are reused (from the next
@@ -299,14 +299,15 @@ et_status et_restore(et_ctx* ctx, const void* in, uint64_t n);
 et_status et_reset(et_ctx* ctx);
 
 /*
- * Serving (cfg.serving): events whose last track died since the previous call, in the
- * order they completed (at most cap; *n receives the number written).  An event is
- * complete when the live-track count its injection raised returns to zero.  The call
- * synchronises the context's stream.
+ * Serving (cfg.serving): events whose last track died since the previous call (at most
+ * cap; *n receives the number written).  An event is complete when it was injected and
+ * none of the current tracks belongs to it: a scan of the active tracks' event fields
+ * between launches finds them, in event-number order.  The call synchronises the
+ * context's stream.
  */
 et_status et_poll_completed(et_ctx* ctx, uint32_t* events, uint64_t cap, uint64_t* n);
 
-/* Serving: clear an event's scores, ledger and live count so that its number can be
+/* Serving: clear an event's scores, ledger and completion state so that its number can be
  * given to a new event (call after reading its results). */
 et_status et_release_event(et_ctx* ctx, uint32_t event);
 

@@ -159,9 +159,10 @@ struct Args {
   uint32_t* heat[NTYPES][2];    // per-word access counts or NULL
   unsigned long long timeout_ns;// bounded waits (persistent driver)
   unsigned long long* iter_ns;  // persistent driver: %globaltimer at each iteration start, or NULL
-  // serving: live tracks per event; an event whose count returns to zero is appended to
-  // the completion ring (NULL: off)
-  int32_t* live;                // [max_events]
+  // serving: events with a track in the current buffers (set by k_mark_present, cleared
+  // by k_scan_done), events injected and not yet reported complete, and the ring of
+  // completed events (NULL: off)
+  uint32_t* present;            // [max_events]
   uint32_t* done_ring;          // [done_cap] completed event ids, position n_done % done_cap
   uint32_t* ev_flag;            // [max_events] 1: injected, completion not yet reported
   uint32_t done_cap;

@@ -208,9 +208,12 @@ static et_status launch(et_ctx* c, const void* fn, int grid, int block, size_t s
   return ET_OK;
 }
 
-// Serving: append the events that have ended since the last scan to the completion ring.
+// Serving: append the events that have ended since the last scan to the completion ring
+// (mark the events of the current tracks, then report the injected ones left unmarked).
 static et_status scan_done(et_ctx* c) {
   void* params[] = {(void*)&c->args};
+  et_status s = launch(c, c->ks.mark_present[c->dense ? 1 : 0], c->num_sms * 4, 256, 0, params);
+  if (s != ET_OK) return s;
   const int grid = (int)((c->cfg.max_events + 255u) / 256u);
   return launch(c, (const void*)k_scan_done, grid < 152 ? grid : 152, 256, 0, params);
 }
@@ -314,11 +317,11 @@ et_status et_create(const et_config* cfg, et_ctx** out) {
     a.idlog_cap = k.id_log_capacity;
   }
   if (k.serving) {
-    a.live = (int32_t*)dalloc(c, (size_t)k.max_events * 4u);
+    a.present = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
     a.done_ring = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
     a.ev_flag = (uint32_t*)dalloc(c, (size_t)k.max_events * 4u);
     a.done_cap = k.max_events;
-    if (!a.live || !a.done_ring || !a.ev_flag) return fail(c, ET_ERR_NOMEM, "serving counters");
+    if (!a.present || !a.done_ring || !a.ev_flag) return fail(c, ET_ERR_NOMEM, "serving counters");
   }
   if (k.reuse_slots && !c->dense) {
     for (int t = 0; t < 3; ++t) {
@@ -376,8 +379,8 @@ et_status et_reset(et_ctx* c) {
   if (a.score)
     CUDA_TRY(c, cudaMemsetAsync(a.score, 0, (size_t)a.max_events * a.n_slabs * 8u, c->stream));
   if (a.trace) CUDA_TRY(c, cudaMemsetAsync(a.trace, 0, 3u * NLEAF * 2u * 8u, c->stream));
-  if (a.live) {
-    CUDA_TRY(c, cudaMemsetAsync(a.live, 0, (size_t)a.max_events * 4u, c->stream));
+  if (a.present) {
+    CUDA_TRY(c, cudaMemsetAsync(a.present, 0, (size_t)a.max_events * 4u, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(a.ev_flag, 0, (size_t)a.max_events * 4u, c->stream));
   }
   c->done_read = 0;
@@ -993,7 +996,7 @@ et_status et_read_counters(et_ctx* c, et_counters* out) {
 
 et_status et_poll_completed(et_ctx* c, uint32_t* events, uint64_t cap, uint64_t* n) {
   if (!c || !n) return ET_ERR_INVALID;
-  if (!c->args.live) return fail(c, ET_ERR_STATE, "not a serving context");
+  if (!c->args.present) return fail(c, ET_ERR_STATE, "not a serving context");
   et_status s = scan_done(c);
   if (s != ET_OK) return s;
   s = sync_ctl(c);
@@ -1025,8 +1028,8 @@ et_status et_release_event(et_ctx* c, uint32_t event) {
   const size_t ns = c->args.n_slabs;
   CUDA_TRY(c, cudaMemsetAsync(c->args.score + (size_t)event * ns, 0, ns * 8u, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->args.ledger + (size_t)event * 5u, 0, 5u * 8u, c->stream));
-  if (c->args.live) {
-    CUDA_TRY(c, cudaMemsetAsync(c->args.live + event, 0, 4u, c->stream));
+  if (c->args.present) {
+    CUDA_TRY(c, cudaMemsetAsync(c->args.present + event, 0, 4u, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->args.ev_flag + event, 0, 4u, c->stream));
   }
   return ET_OK;
@@ -1155,8 +1158,8 @@ static std::vector<SnapItem> snapshot_items(et_ctx* c) {
   v.push_back({SN_SCORE, 0, a.score, (uint64_t)a.max_events * a.n_slabs * 8u});
   v.push_back({SN_LEDGER, 0, a.ledger, (uint64_t)a.max_events * 5u * 8u});
   v.push_back({SN_COUNTS, 0, a.counts_log, (uint64_t)a.max_iters * 12u});
-  if (a.live) {
-    v.push_back({SN_LIVE, 0, a.live, (uint64_t)a.max_events * 4u});
+  if (a.present) {
+    v.push_back({SN_LIVE, 0, a.present, (uint64_t)a.max_events * 4u});
     v.push_back({SN_DONE, 0, a.done_ring, (uint64_t)a.done_cap * 4u});
     v.push_back({SN_EVFLAG, 0, a.ev_flag, (uint64_t)a.max_events * 4u});
   }
@@ -1266,7 +1269,7 @@ et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
       case SN_SCORE: dev = a.score; limit = (uint64_t)a.max_events * a.n_slabs * 8u; break;
       case SN_LEDGER: dev = a.ledger; limit = (uint64_t)a.max_events * 40u; break;
       case SN_COUNTS: dev = a.counts_log; limit = (uint64_t)a.max_iters * 12u; break;
-      case SN_LIVE: dev = a.live; limit = (uint64_t)a.max_events * 4u; break;
+      case SN_LIVE: dev = a.present; limit = (uint64_t)a.max_events * 4u; break;
       case SN_DONE: dev = a.done_ring; limit = (uint64_t)a.done_cap * 4u; break;
       case SN_EVFLAG: dev = a.ev_flag; limit = (uint64_t)a.max_events * 4u; break;
       case SN_IDLOG: dev = a.idlog; limit = a.idlog_cap * sizeof(IdRec); break;
@@ -1300,7 +1303,7 @@ et_status et_restore(et_ctx* c, const void* in, uint64_t n) {
 // it and hands back that round's results: the host's admission and read-back overlap the
 // GPU's work on the next round, which is already queued on the stream.
 static et_status serve_state(et_ctx* c, ServeState** out) {
-  if (!c->args.live) return fail(c, ET_ERR_STATE, "not a serving context");
+  if (!c->args.present) return fail(c, ET_ERR_STATE, "not a serving context");
   if (!c->have_geom || !c->have_tables || (c->cfg.msc && !c->have_msc))
     return fail(c, ET_ERR_STATE, "geometry, tables (and radiation lengths for msc) first");
   if (!c->serve) {

@@ -467,24 +467,6 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
       }
     }
   }
-  // serving: live-track count of the event (an event whose count is back to zero has
-  // ended; k_scan_done reports it between launches).  The warp's lanes of one event add
-  // their changes first (a ballot per event, an integer warp reduction), and the sum goes
-  // out as a reduction that nothing waits for: a few events in flight would otherwise see
-  // one atomic round trip per lane on a handful of counters.
-  if (a.live) {
-    const int delta = act ? (o.alive ? 1 : 0) + nsec - 1 : 0;
-    uint32_t pend = __ballot_sync(FULL, delta != 0);
-    while (pend) {
-      const int src = __ffs(pend) - 1;
-      const uint32_t ev = __shfl_sync(FULL, t.event, src);
-      const uint32_t grp = __ballot_sync(FULL, delta != 0 && t.event == ev) & pend;
-      const int sum = __reduce_add_sync(FULL, ((grp >> lane) & 1u) ? delta : 0);
-      if ((int)lane == src && sum != 0)
-        asm volatile("red.global.add.s32 [%0], %1;" ::"l"(a.live + ev), "r"(sum) : "memory");
-      pend &= ~grp;
-    }
-  }
 }
 
 // One warp transports up to 32 tracks of one type (lanes with valid == false idle).
@@ -757,16 +739,18 @@ __global__ void k_end_iteration(const __grid_constant__ Args a, cudaGraphConditi
 
 #ifdef ET_HOST_TU
 // ---- serving: report the events whose last track has died ----
-// Between launches (every step has been counted): an event that was injected and whose
-// live-track count is back to zero is appended to the completion ring, once.
+// Between launches, after k_mark_present: an event that was injected and has no track
+// in the current buffers is appended to the completion ring, once; the presence flags
+// are cleared for the next scan.
 __global__ void k_scan_done(const __grid_constant__ Args a) {
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < a.max_events;
        e += gridDim.x * blockDim.x) {
-    if (a.ev_flag[e] != 0u && a.live[e] == 0) {
+    if (a.ev_flag[e] != 0u && a.present[e] == 0u) {
       a.ev_flag[e] = 0u;
       const uint32_t pos = atomicAdd(&a.ctl->n_done, 1u);
       a.done_ring[pos % a.done_cap] = e;
     }
+    a.present[e] = 0u;
   }
 }
 
@@ -781,9 +765,8 @@ __global__ void k_round_stop(const __grid_constant__ Args a, uint32_t rel) {
 // One block.  For at most max_out completions after *cursor (the completion ring is
 // final: every iteration before this kernel has ended), copies the event's per-slab
 // deposits and its ledger to out_rows[j] ([n_slabs + 5] doubles) and its number to
-// out_events[j], clears the event's scores, ledger and live count (its number can be
-// given to a new event afterwards), advances the cursor and writes the count to
-// out_events[max_out].
+// out_events[j], clears the event's scores and ledger (its number can be given to a new
+// event afterwards), advances the cursor and writes the count to out_events[max_out].
 __global__ void k_serve_collect(const __grid_constant__ Args a, uint32_t* cursor,
                                 uint32_t* out_events, double* out_rows, uint32_t max_out) {
   const uint32_t cur = *cursor;
@@ -803,10 +786,7 @@ __global__ void k_serve_collect(const __grid_constant__ Args a, uint32_t* cursor
         lg[i - ns] = 0.0;
       }
     }
-    if (threadIdx.x == 0) {
-      out_events[j] = e;
-      a.live[e] = 0;
-    }
+    if (threadIdx.x == 0) out_events[j] = e;
   }
   if (threadIdx.x == 0) {
     *cursor = cur + n;
@@ -1026,6 +1006,33 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
   }
 }
 
+// ---- serving: which events still have tracks ----
+// Between launches: every track of the current iteration marks its event present (plain
+// stores of 1: idempotent).  A scan of the event field of the active tracks -- 4 bytes a
+// track, coalesced -- replaces per-step live-track counting in the step kernels, whose
+// atomics on the few counters of the events in flight cost more than the whole scan.
+template <int L, bool DENSE>
+__global__ void k_mark_present(const __grid_constant__ Args a) {
+  const DevCtl* c = a.ctl;
+  const uint32_t it = c->iter;
+  const uint32_t hc = it & 1u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (int t = 0; t < NTYPES; ++t) {
+    uint32_t n = c->cnt[it % 3][cw(t)];
+    n = n < a.cap ? n : a.cap;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      uint32_t ev;
+      if constexpr (DENSE) {
+        ev = view_of<L, false>(a, t, (int)hc).template ld<uint32_t>(i, F_EVENT);
+      } else {
+        const uint32_t slot = __ldcg(idx_of(a, t, (int)hc) + i);
+        ev = view_of<L, false>(a, t, 0).template ld<uint32_t>(slot, F_EVENT);
+      }
+      if (ev < a.max_events) a.present[ev] = 1u;
+    }
+  }
+}
+
 // ---- injection of primaries into the current iteration's tracks ----
 struct Primary {
   uint32_t type, event;
@@ -1072,10 +1079,7 @@ __global__ void k_inject(const __grid_constant__ Args a, const Primary* p, uint3
     t.len = 0.0f;
     t.flags = 0;
     atomicAdd(&a.ledger[(size_t)t.event * 5 + 0], (double)t.e);
-    if (a.live) {
-      atomicAdd(&a.live[t.event], 1);
-      a.ev_flag[t.event] = 1u;
-    }
+    if (a.ev_flag) a.ev_flag[t.event] = 1u;
   }
   const uint32_t packed = ok ? (1u << (10 * type)) : 0u;
   uint32_t q0, q1, q2;

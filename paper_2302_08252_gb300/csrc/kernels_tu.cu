@@ -50,6 +50,8 @@ extern "C" void ET_CAT(ET_MODE, ET_LAYOUT)(et::KernelSet* ks) {
 #endif
   ks->inject[1] = (const void*)et::k_inject<ET_LAYOUT, true>;
   ks->inject[0] = (const void*)et::k_inject<ET_LAYOUT, false>;
+  ks->mark_present[1] = (const void*)et::k_mark_present<ET_LAYOUT, true>;
+  ks->mark_present[0] = (const void*)et::k_mark_present<ET_LAYOUT, false>;
   et::fill_split<true>(ks);
   et::fill_split<false>(ks);
 }

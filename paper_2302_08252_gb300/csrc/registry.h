@@ -8,6 +8,7 @@ struct KernelSet {
   const void* step[2][2][3];     // [instrumented][dense][type]
   const void* persistent[2][2];  // [instrumented][dense]
   const void* inject[2];         // [dense]
+  const void* mark_present[2];   // [dense] serving: events with tracks in the buffers
   const void* transport[2][3];   // split form, not instrumented: [dense][type]
   const void* interact[2][3];    // split form, not instrumented: [dense][type]
 };
