@@ -223,8 +223,10 @@ __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const St
   }
 }
 
-// warp-aggregated append of death records
-__device__ __forceinline__ void log_deaths(const Args& a, bool dead, const Trk& t, int type,
+// warp-aggregated append of death records; out of line, since only test runs keep the
+// log and the hot loop should not carry its code (+2 % on the single shower, +0.6 % on
+// the batched events)
+static __device__ __noinline__ void log_deaths(const Args& a, bool dead, const Trk& t, int type,
                                            int death, uint32_t lane) {
   const uint32_t mask = __ballot_sync(FULL, dead);
   if (!mask) return;
