@@ -8,9 +8,10 @@ library's native serving loop (et_serve_submit / et_serve_round, include/et.h):
      type); the library admits queued events in order while their reserves fit the free
      track-buffer capacity (admission by memory) and injects them;
   2. each round runs a few transport iterations with every shower in flight (new ones
-     start while the others go on: their work overlaps on the device), and a device
-     kernel collects the events whose last track died (device-side live-track counters)
-     -- their per-layer deposits and ledgers -- into one buffer copied to pinned memory;
+     start while the others go on: their work overlaps on the device); after the round
+     a scan of the active tracks marks the events that still have one, and a device
+     kernel collects the events that have none left -- their per-layer deposits and
+     ledgers -- into one buffer copied to pinned memory;
   3. a round returns the completions of the round before it: the GPU is already running
      the next round while the host admits and reads back.
 
@@ -94,7 +95,8 @@ def reserve(primaries: np.ndarray) -> np.ndarray:
 class Server:
     def __init__(self, geom: dict, form: str = "dense", layout: str = "aos",
                  driver: str = "persistent", capacity_log2: int = 22, max_events: int = 1 << 14,
-                 iters_per_round: int = 16, seed: int = 1, tables: dict | None = None):
+                 iters_per_round: int = 16, seed: int = 1, tables: dict | None = None,
+                 **ctx_kw):
         self.geom = geom
         self.n_slabs = len(geom["thickness"])
         self.capacity = 1 << capacity_log2
@@ -103,7 +105,7 @@ class Server:
                                    capacity_log2=capacity_log2,
                                    form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
                                    layout=layout, driver=driver, seed=seed, serving=True,
-                                   reuse_slots=(form == "sparse"))
+                                   reuse_slots=(form == "sparse"), **ctx_kw)
         self.buf = et.ServeBuffers(self.ctx, self.n_slabs)
 
     def _collect(self, out, stats, submitted, t_done):

@@ -33,13 +33,17 @@ def _close(a, b):
     return np.all(np.abs(a - b) <= DEPOSIT_RTOL * np.abs(b) + 1e-9)
 
 
-@pytest.mark.parametrize("form", ["dense", "sparse"])
-def test_each_event_same_alone_and_in_the_mix(geom, form):
+@pytest.mark.parametrize("form,driver", [("dense", "persistent"), ("sparse", "persistent"),
+                                         ("dense", "hybrid")])
+def test_each_event_same_alone_and_in_the_mix(geom, form, driver):
+    # the hybrid driver with a low switch-over population runs the large rounds in the
+    # graph of per-type step kernels
     from paper_2302_08252_gb300 import et, serving
     n_ev = 40
     reqs = _requests(n_ev, rate=2000.0)
+    kw = {"hybrid_tracks": 1 << 12} if driver == "hybrid" else {}
     srv = serving.Server(geom, form=form, layout="aosoa32" if form == "dense" else "aos",
-                         driver="persistent", capacity_log2=20, max_events=64, iters_per_round=8)
+                         driver=driver, capacity_log2=20, max_events=64, iters_per_round=8, **kw)
     st = srv.serve(reqs, realtime=True)
     assert len(st.results) == n_ev and sorted(r.event for r in st.results) == list(range(n_ev))
     assert st.max_inflight > 1          # requests overlapped on the device
