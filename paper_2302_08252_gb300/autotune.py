@@ -118,8 +118,8 @@ def main(argv=None):
     tuned = autotune(geom, prim, n_events, sample=a.sample, reps=a.reps,
                      capacity_log2=min(a.capacity_log2, 24))  # a sample needs fewer slots
     b = tuned["best"]
-    steps = study.steps_of(geom, prim, n_events, "dense", b["layout"], b["driver"],
-                           a.capacity_log2)
+    steps, _ = study.steps_of(geom, prim, n_events, "dense", b["layout"], b["driver"],
+                              a.capacity_log2)
     full = []
     for layout, block, driver in [(b["layout"], b["block_size"], b["driver"]),
                                   ("aosoa32", 256, "persistent"), ("aosoa32", 256, "graph"),

@@ -223,29 +223,39 @@ __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const St
   }
 }
 
-// warp-aggregated append of death records; out of line, since only test runs keep the
-// log and the hot loop should not carry its code (+2 % on the single shower, +0.6 % on
-// the batched events)
-static __device__ __noinline__ void log_deaths(const Args& a, bool dead, const Trk& t, int type,
-                                           int death, uint32_t lane) {
+// Warp-aggregated append of death records (test runs only).  Two entry points: inline,
+// and out of line so that a kernel need not carry the code in its hot loop.  The
+// arguments are scalars: a track passed by reference would have to sit in local memory
+// around the call.  Which one a kernel uses is chosen by what it spills: the electron
+// step kernel, at 64 registers, spills around the call and not with the inline code;
+// the photon and positron kernels, and the all-type persistent kernel, run faster with
+// the call (+1.9 % and +2.1 % on the batched events, +2 % on the single shower).
+__device__ __forceinline__ void log_deaths_inl(IdRec* log, unsigned long long cap, DevCtl* ctl,
+                                               bool dead, unsigned long long id, uint32_t steps,
+                                               uint32_t type_death, uint32_t lane) {
   const uint32_t mask = __ballot_sync(FULL, dead);
   if (!mask) return;
   unsigned long long base = 0;
   const uint32_t leader = __ffs(mask) - 1;
-  if (lane == leader) base = atomicAdd(&a.ctl->idlog_n, (unsigned long long)__popc(mask));
+  if (lane == leader) base = atomicAdd(&ctl->idlog_n, (unsigned long long)__popc(mask));
   base = __shfl_sync(FULL, base, leader);
   if (dead) {
     const unsigned long long at = base + __popc(mask & ((1u << lane) - 1u));
-    if (at < a.idlog_cap) {
+    if (at < cap) {
       IdRec r;
-      r.id = t.id;
-      r.steps = t.step;
-      r.type_death = (uint32_t)type | ((uint32_t)death << 8);
-      a.idlog[at] = r;
+      r.id = id;
+      r.steps = steps;
+      r.type_death = type_death;
+      log[at] = r;
     } else {
-      atomicOr(&a.ctl->status, ST_LOG_FULL);
+      atomicOr(&ctl->status, ST_LOG_FULL);
     }
   }
+}
+static __device__ __noinline__ void log_deaths(IdRec* log, unsigned long long cap, DevCtl* ctl,
+                                               bool dead, unsigned long long id, uint32_t steps,
+                                               uint32_t type_death, uint32_t lane) {
+  log_deaths_inl(log, cap, ctl, dead, id, steps, type_death, lane);
 }
 
 // Per-lane tallies of secondaries per type and sampler-cap hits, kept in registers and
@@ -386,7 +396,7 @@ __device__ __forceinline__ void q_get(const uint32_t* q, LD ld, uint32_t s, Trk&
 // deposits, death records, counters, slot allocation and the writes of the survivor
 // and the secondaries.  All 32 lanes of the warp call it together; `type` is
 // warp-uniform.
-template <int L, bool INSTR, bool DENSE>
+template <int L, bool INSTR, bool DENSE, bool INLINE_LOG>
 __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t it, uint32_t lane,
                                        bool act, const Trk& t, const StepOut& o, uint32_t slot,
                                        Tally& tl) {
@@ -396,7 +406,15 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
   if (act) score_step(a, t, o);
   const bool alive = act && o.alive;
   const int nsec = act ? o.nsec : 0;
-  if (a.idlog) log_deaths(a, act && !o.alive, t, type, act ? o.death : 0, lane);
+  if (a.idlog) {
+    const uint32_t td = (uint32_t)type | ((uint32_t)(act ? o.death : 0) << 8);
+    if (INLINE_LOG)
+      log_deaths_inl(a.idlog, a.idlog_cap, a.ctl, act && !o.alive, (unsigned long long)t.id,
+                     t.step, td, lane);
+    else
+      log_deaths(a.idlog, a.idlog_cap, a.ctl, act && !o.alive, (unsigned long long)t.id, t.step,
+                 td, lane);
+  }
 
   // per-type record counts of this lane: survivor + secondaries
   uint32_t packed_sec = 0;
@@ -481,7 +499,7 @@ __device__ __forceinline__ void finish(const Args& a, const int type, uint32_t i
 // its rejection loop divergent, while a bremsstrahlung emission is short enough that
 // parking it costs more than the idle lanes it saves (measured: 3 % on the persistent
 // kernel, 5 % on the per-type kernels of the batched events).
-template <int MODE, int L, bool INSTR, bool DENSE>
+template <int MODE, int L, bool INSTR, bool DENSE, bool INLINE_LOG>
 __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, const int type,
                                              uint32_t it, uint32_t i, bool valid, uint32_t lane,
                                              WarpQueue& wq, bool batch, bool drain_all, Tally& tl) {
@@ -528,7 +546,7 @@ __device__ __forceinline__ void process_warp(const Args& a, const Tabs& tb, cons
     }
     if (do_int) interact<MODE>(type, t, cx, a.seed_lo, o, a.msc != 0);
     if (!once) __syncwarp();  // entries consumed before their ring slots are reused
-    finish<L, INSTR, DENSE>(a, type, it, lane, act, t, o, s2, tl);
+    finish<L, INSTR, DENSE, INLINE_LOG>(a, type, it, lane, act, t, o, s2, tl);
     if (!once) {
       wq.head = (wq.head + n) % QCAP;
       wq.count -= n;
@@ -574,8 +592,8 @@ __global__ void __launch_bounds__(256, DENSE ? (TYPE == EM ? 4 : 3) : 1) k_step(
     const bool more = c < chunks;
     const uint32_t i = c * 32u + lane;
     const bool last = !more || c + nw >= chunks;
-    process_warp<MODE, L, INSTR, DENSE>(a, tb, TYPE, it, i, more && i < n, lane, wq, batch,
-                                        last, tl);
+    process_warp<MODE, L, INSTR, DENSE, TYPE == EM>(a, tb, TYPE, it, i, more && i < n, lane,
+                                                    wq, batch, last, tl);
     c += nw;
   }
   tally_flush(a, tl, lane);
@@ -646,7 +664,7 @@ __global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_transport(const __grid_c
       }
       inter = transport<MODE>(TYPE, t, tb, a.log_emin, a.inv_dlog, a.half_xy, a.seed_lo, o, cx);
     }
-    finish<L, false, DENSE>(a, TYPE, it, lane, valid && !inter, t, o, slot, tl);
+    finish<L, false, DENSE, false>(a, TYPE, it, lane, valid && !inter, t, o, slot, tl);
     // queue positions: one ballot per queue (a lane enters at most one), then one
     // atomicAdd per non-empty queue
     const int k = (TYPE == GAM && inter) ? photon_queue(cx) - IQ_COMPTON : 0;
@@ -707,7 +725,7 @@ __global__ void __launch_bounds__(256, DENSE ? 3 : 1) k_interact(const __grid_co
       q_get(queue_of<TYPE>(a, k), (size_t)a.cap, p, t, cx, slot);
       interact<MODE>(TYPE, t, cx, a.seed_lo, o, a.msc != 0);
     }
-    finish<L, false, DENSE>(a, TYPE, it, lane, act, t, o, slot, tl);
+    finish<L, false, DENSE, false>(a, TYPE, it, lane, act, t, o, slot, tl);
   }
   tally_flush(a, tl, lane);
 }
@@ -991,7 +1009,8 @@ __global__ void __launch_bounds__(256, 3) k_persistent(const __grid_constant__ A
         }
         // else: drain the previous type's queue first; this chunk is taken next round
       }
-      process_warp<MODE, L, INSTR, DENSE>(a, tb, ty, it, i, valid, lane, wq, batch, drain_all, tl);
+      process_warp<MODE, L, INSTR, DENSE, false>(a, tb, ty, it, i, valid, lane, wq, batch,
+                                                 drain_all, tl);
     }
     if (!grid_sync(c, gridDim.x, a.timeout_ns, bar_gen, a.free_ring[0] != nullptr, &s_snap_stop))
       return;

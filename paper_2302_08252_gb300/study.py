@@ -41,13 +41,15 @@ def workload(name: str):
     raise ValueError(name)
 
 
-def steps_of(geom, primaries, n_events, form, layout, driver, capacity_log2, **ctx_kw) -> int:
+def steps_of(geom, primaries, n_events, form, layout, driver, capacity_log2, **ctx_kw):
+    """Track-steps of one complete run: the total and the per-type counts (e-, e+, gamma)."""
     from . import et
     ctx = et.make_context(geom, max_events=n_events, capacity_log2=capacity_log2,
                           form=et.FORM_DENSE if form == "dense" else et.FORM_SPARSE,
                           layout=layout, driver=driver, **ctx_kw)
     et.et_inject(ctx, primaries)
-    return int(et.et_run_until_empty(ctx)["steps"])
+    total = int(et.et_run_until_empty(ctx)["steps"])
+    return total, [int(x) for x in et.et_read_counters(ctx)["steps"]]
 
 
 def main(argv=None):
@@ -68,7 +70,7 @@ def main(argv=None):
     geom = W.calorimeter()
     prim, n_events = workload(a.workload)
     rows = []
-    steps = None
+    steps = by_type = None
     for form in a.forms:
         cap = a.dense_capacity_log2 if form == "dense" else a.sparse_capacity_log2
         for layout in a.layouts:
@@ -81,13 +83,15 @@ def main(argv=None):
                     if driver == "hybrid":
                         kw["hybrid_tracks"] = 1 << tk
                     if steps is None:
-                        steps = steps_of(geom, prim, n_events, form, layout, driver, cap, **kw)
+                        steps, by_type = steps_of(geom, prim, n_events, form, layout, driver, cap,
+                                                  **kw)
                     t = autotune.time_config(geom, prim, n_events, form, layout, a.block_size,
                                              driver, reps=a.reps, capacity_log2=cap, **kw)
                     r = {"workload": a.workload, "form": form, "layout": layout,
                          "driver": driver, "split": bool(split), "block_size": a.block_size,
                          "hybrid_tracks": kw.get("hybrid_tracks", 0),
-                         "seconds": t, "steps": steps, "track_steps_per_s": steps / t}
+                         "seconds": t, "steps": steps, "steps_by_type": by_type,
+                         "track_steps_per_s": steps / t}
                     rows.append(r)
                     print(json.dumps(r), flush=True)
     if a.out:
