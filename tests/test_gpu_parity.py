@@ -72,6 +72,31 @@ def test_run_iteration_steps_one_at_a_time(geom, small_ref):
     assert counts == [int(x) for x in o["counts"].sum(1)]
 
 
+def test_score_reads_agree(geom, small_ref):
+    """Scores read one event at a time, all at once and a second time give the same
+    values; events injected after a completed run and a read add their deposits to their
+    own rows; everything matches the oracle."""
+    from paper_2302_08252_gb300 import et
+    p, o = small_ref
+    ns = len(geom["thickness"])
+    ctx = et.make_context(geom, max_events=16, capacity_log2=16, form=et.FORM_DENSE,
+                          driver="persistent")
+    et.et_inject(ctx, p[p["event"] < 8])
+    et.et_run_until_empty(ctx)
+    first, _ = et.et_read_scoring_all(ctx, 16, ns)
+    et.et_inject(ctx, p[p["event"] >= 8])   # a second batch adds to the folded scores
+    et.et_run_until_empty(ctx)
+    all1, _ = et.et_read_scoring_all(ctx, 16, ns)
+    all2, _ = et.et_read_scoring_all(ctx, 16, ns)
+    assert np.array_equal(all1, all2)
+    assert np.array_equal(all1[:8], first[:8])
+    for ev in (0, 9, 15):
+        dep, _ = et.et_read_scoring(ctx, ev, ns)
+        assert np.array_equal(dep, all1[ev])
+    ref = o["score"]
+    assert np.all(np.abs(all1 - ref) <= 1e-6 * np.abs(ref) + 1e-9)
+
+
 def test_full_jittered_electrons(geom):
     """1,000 x 10 GeV electrons, dense AoSoA-32, persistent driver: all outputs vs oracle."""
     p = W.jittered_electrons()
