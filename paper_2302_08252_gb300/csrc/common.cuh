@@ -127,6 +127,16 @@ struct IdRec {
   uint32_t type_death;
 };
 
+// Column of slab s in an event's row of deposits (ns slabs).  Within each complete group
+// of 32 slabs, slabs alternate between the group's two 128-byte halves (s -> 16 (s mod 2)
+// + (s mod 32) / 2), so that the adjacent slabs of a shower's maximum, which take most
+// of its deposits, fall on different L2 lines; a shower still touches the same few lines
+// of its row.  The last, incomplete group keeps its order.  A bijection on [0, ns).
+__host__ __device__ __forceinline__ uint32_t score_col(uint32_t s, uint32_t ns) {
+  const uint32_t g = s & ~31u;
+  return g + 32u <= ns ? g + ((s & 1u) << 4) + ((s & 31u) >> 1) : s;
+}
+
 // ---- kernel arguments (passed by value) ----
 struct Args {
   char* trk[NTYPES][2];         // dense: [type][half]; sparse: [type][0]
@@ -139,7 +149,8 @@ struct Args {
   uint32_t hybrid_t;             // hybrid driver: the persistent kernel stops before an iteration
                                  // with this many tracks, the graph before one with fewer (0: off)
   uint32_t n_slabs;
-  double* score;                // [max_events][n_slabs]
+  double* score;                // [max_events][n_slabs], columns in score_col order
+  uint32_t score_il;            // 1: slabs interleaved in each row (score_col), 0: in order
   double* ledger;               // [max_events][5]: injected, cut, escaped, mass_created, mass_consumed
   uint32_t max_events;
   uint32_t n_mat;

@@ -434,6 +434,7 @@ et_status et_create_geometry(et_ctx* c, uint32_t n_slabs, const double* thicknes
   a.planes = dp;
   a.mat = dm;
   a.score = sc;
+  a.score_il = 1u;
   a.n_slabs = n_slabs;
   a.half_xy = half_xy_mm;
   c->planes = planes;
@@ -876,9 +877,11 @@ et_status et_read_scoring(et_ctx* c, uint32_t event, double* slab_dep, size_t n_
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
   double sum = 0.0;
-  for (size_t i = 0; i < sc.size(); ++i) {
-    if (slab_dep) slab_dep[i] = sc[i];
-    sum += sc[i];
+  const uint32_t ns = c->args.n_slabs;
+  for (uint32_t i = 0; i < ns; ++i) {
+    const double v = sc[c->args.score_il ? score_col(i, ns) : i];
+    if (slab_dep) slab_dep[i] = v;
+    sum += v;
   }
   if (out) {
     out->injected = lg[0];
@@ -912,6 +915,14 @@ et_status et_read_scoring_all(et_ctx* c, double* score, et_ledger* ledger) {
     CUDA_TRY(c, cudaMemcpyAsync(c->h_ledger, c->args.ledger, ne * 5 * 8, cudaMemcpyDeviceToHost, c->stream));
   et_status s = sync_ctl(c);
   if (s != ET_OK) return s;
+  if (dst && c->args.score_il) {  // rows back into slab order
+    double row[MAX_SLABS];
+    for (size_t e = 0; e < ne; ++e) {
+      double* r = dst + e * ns;
+      memcpy(row, r, ns * sizeof(double));
+      for (uint32_t i = 0; i < (uint32_t)ns; ++i) r[i] = row[score_col(i, (uint32_t)ns)];
+    }
+  }
   if (ledger) {
     for (size_t e = 0; e < ne; ++e) {
       double sum = 0.0;

@@ -211,10 +211,12 @@ __device__ __forceinline__ void red_add(double* p, double v) {
 
 __device__ __forceinline__ void score_step(const Args& a, const Trk& t, const StepOut& o) {
   const size_t ev = t.event;
-  if (o.dep_nz) red_add(&a.score[ev * a.n_slabs + (size_t)o.slab_cont], o.dep);
+  const uint32_t c0 = a.score_il ? score_col((uint32_t)o.slab_cont, a.n_slabs) : (uint32_t)o.slab_cont;
+  if (o.dep_nz) red_add(&a.score[ev * a.n_slabs + c0], o.dep);
   if (o.bal) {
     if ((o.bal & B_CUT) && o.cut != 0.0) {
-      red_add(&a.score[ev * a.n_slabs + (size_t)t.slab], o.cut);
+      const uint32_t c1 = a.score_il ? score_col((uint32_t)t.slab, a.n_slabs) : (uint32_t)t.slab;
+      red_add(&a.score[ev * a.n_slabs + c1], o.cut);
       red_add(&a.ledger[ev * 5 + 1], o.cut);
     }
     if ((o.bal & B_ESC) && o.esc != 0.0f) red_add(&a.ledger[ev * 5 + 2], f2d(o.esc));
@@ -784,7 +786,7 @@ __global__ void k_round_stop(const __grid_constant__ Args a, uint32_t rel) {
 // ---- serving: collect the events completed since the last collection ----
 // One block.  For at most max_out completions after *cursor (the completion ring is
 // final: every iteration before this kernel has ended), copies the event's per-slab
-// deposits and its ledger to out_rows[j] ([n_slabs + 5] doubles) and its number to
+// deposits (in slab order) and its ledger to out_rows[j] ([n_slabs + 5] doubles) and its number to
 // out_events[j], clears the event's scores and ledger (its number can be given to a new
 // event afterwards), advances the cursor and writes the count to out_events[max_out].
 __global__ void k_serve_collect(const __grid_constant__ Args a, uint32_t* cursor,
@@ -799,8 +801,9 @@ __global__ void k_serve_collect(const __grid_constant__ Args a, uint32_t* cursor
     double* lg = a.ledger + (size_t)e * 5u;
     for (uint32_t i = threadIdx.x; i < row; i += blockDim.x) {
       if (i < ns) {
-        out_rows[(size_t)j * row + i] = sc[i];
-        sc[i] = 0.0;
+        const uint32_t col = a.score_il ? score_col(i, ns) : i;
+        out_rows[(size_t)j * row + i] = sc[col];
+        sc[col] = 0.0;
       } else {
         out_rows[(size_t)j * row + i] = lg[i - ns];
         lg[i - ns] = 0.0;
