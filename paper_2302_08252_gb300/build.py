@@ -1,7 +1,7 @@
 """Build the CUDA library libet.so in-tree for sm_103a.
 
-Eight kernel objects (strict/fast mode x AoS/SoA/AoSoA-32/AoSoA-64 layout)
-from one source, the C ABI host object and the table builder, compiled in
+Sixteen kernel objects (strict/fast mode x the eight track layouts) from one
+source, the C ABI host objects and the table builder, compiled in
 parallel and linked into paper_2302_08252_gb300/_build/libet.so.  Strict
 objects use --fmad=false with IEEE division/square root and no flush to zero;
 host code uses -ffp-contract=off (the toy model fixes every rounding).

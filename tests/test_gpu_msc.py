@@ -63,7 +63,8 @@ def test_mixed_types_bit_exact(geom):
 
 def test_full_jittered_electrons(geom):
     """The whole 1,000 x 10 GeV shower under v2 (about 290 M track-steps), dense form,
-    the autotuner's layout and the hybrid driver: everything but the death records."""
+    AoSoA-64 and the hybrid driver (AoSoA-32 is covered by the small cases): everything
+    but the death records."""
     p = W.jittered_electrons()
     o = oracle_run(geom, p, 1000, idlog=False, nthreads=16, msc=True)
     g = run_gpu(geom, p, 1000, form="dense", layout="aosoa64", driver="hybrid",
