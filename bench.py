@@ -456,7 +456,8 @@ def ours_arm(args, rank, world, group):
         runs_per_launch = args.steps / tuned["kernel_launches"]
         alg_per_launch = algorithmic_bytes(steps_per_run, tuned["n_prim"]) * runs_per_launch
         achieved = alg_per_launch / (per_launch_ms / 1e3) / 1e9
-    key = f"{args.mode}/{args.form}/{args.layout}/{args.driver}" + ("/msc" if args.msc else "")
+    key = (f"{args.workload}/{args.mode}/{args.form}/{args.layout}/{args.driver}" +
+           ("/msc" if args.msc else ""))
     tr = committed_traffic(key)
     traffic = tr * steps_per_run * (args.steps / max(1, tuned["kernel_launches"])) if tr else None
 
