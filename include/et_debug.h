@@ -43,6 +43,15 @@ enum { ET_EVAL_PHILOX = 0, ET_EVAL_U01 = 1, ET_EVAL_LOG = 2, ET_EVAL_EXP = 3, ET
 et_status et_debug_eval(int what, const void* in_device, void* out_device, size_t n,
                         void* cuda_stream);
 
+/*
+ * The column of each slab in an event's row of the device deposit array (out[s] for
+ * s < n_slabs; 1 <= n_slabs <= 128): within each complete group of 32 slabs, adjacent
+ * slabs sit in the group's two 128-byte halves alternately; an incomplete last group
+ * keeps its order.  The read calls return deposits in slab order; this only exposes
+ * the device layout to tests.  Host only; ET_ERR_INVALID for a bad count or null out.
+ */
+et_status et_debug_score_columns(uint32_t n_slabs, uint32_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1096,6 +1096,13 @@ et_status et_debug_set_barrier_fault(et_ctx* c, int skip_block, uint64_t timeout
 }
 
 
+// Test hook (et_debug.h): the deposit rows' column order.
+et_status et_debug_score_columns(uint32_t n_slabs, uint32_t* out) {
+  if (!out || n_slabs < 1 || n_slabs > (uint32_t)MAX_SLABS) return ET_ERR_INVALID;
+  for (uint32_t s = 0; s < n_slabs; ++s) out[s] = score_col(s, n_slabs);
+  return ET_OK;
+}
+
 // Test hook (et_debug.h): the device primitives on a batch of inputs.
 et_status et_debug_eval(int what, const void* in, void* out, size_t n, void* stream) {
   if (what < ET_EVAL_PHILOX || what > ET_EVAL_SINCOS2PI || (n && (!in || !out)))

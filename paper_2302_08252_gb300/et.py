@@ -122,6 +122,7 @@ def _load():
                                   C.POINTER(C.c_uint64), vp, C.c_char_p, C.c_size_t], st),
         "et_debug_set_barrier_fault": ([vp, C.c_int, C.c_uint64], st),
         "et_debug_eval": ([C.c_int, vp, vp, C.c_size_t, vp], st),
+        "et_debug_score_columns": ([C.c_uint32, vp], st),
         "et_debug_iteration_times": ([vp, C.c_int], st),
         "et_debug_read_iteration_times": ([vp, vp, C.c_uint64, C.POINTER(C.c_uint64)], st),
     }

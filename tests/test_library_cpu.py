@@ -90,6 +90,29 @@ def test_invalid_config_rejected(libet):
     assert not h.value
 
 
+def test_score_columns_interleave_each_32_slab_group(libet):
+    """The deposit rows' column order (host mirror of the device's): a permutation of the
+    slabs; within a complete group of 32, slab s sits at 16 (s mod 2) + (s mod 32) / 2,
+    so neighbouring slabs are 16 doubles (one 128-byte half) apart; the last incomplete
+    group keeps its order; bad counts are refused."""
+    out = (ctypes.c_uint32 * 128)()
+    for ns in range(1, 129):
+        assert libet.et_debug_score_columns(ns, out) == 0
+        col = list(out)[:ns]
+        assert sorted(col) == list(range(ns))
+        full = (ns // 32) * 32
+        for s in range(full):
+            assert col[s] == (s & ~31) + 16 * (s & 1) + (s & 31) // 2
+        for s in range(full, ns):
+            assert col[s] == s
+        for s in range(full - 1):
+            if (s + 1) % 32:
+                assert abs(col[s + 1] - col[s]) in (15, 16)
+    assert libet.et_debug_score_columns(0, out) == 1
+    assert libet.et_debug_score_columns(129, out) == 1
+    assert libet.et_debug_score_columns(4, None) == 1
+
+
 def test_aosoa128_needs_a_full_block(libet):
     from paper_2302_08252_gb300 import et
     cfg = et.et_config()
